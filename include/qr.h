@@ -1,0 +1,198 @@
+/*
+ * qr.h -- C-ABI of libqrmc, a B300 (sm_103a) implementation of the
+ * Quasi-Regression Monte-Carlo (QRMC) scheme of Gobet, Lopez-Salas and
+ * Vazquez, "Quasi-Regression Monte-Carlo scheme for semi-linear PDEs and
+ * BSDEs with large scale parallelization on GPUs" (arXiv 2407.21084).
+ *
+ * The library solves the dynamic programming equation of Sec. 2.1.1,
+ *     y_i(x) = E[ g(X_N) + sum_{j=i}^{N-1} f(t_j, X_j, y_{j+1}(X_{j+1})) dt | X_i = x ],
+ * on the grid t_j = j dt, dt = T/N, with X the Euler scheme of Sec. 2.1.1
+ * (constant drift b and constant diffusion matrix sigma). Each y_i is
+ * represented by its coefficients alpha_{i,k}, k in an index set Gamma of
+ * Z^d, on the nu-orthonormal basis phi_k(x) = prod_l e^{2 pi i k_l F_nu(x_l)}
+ * (Sec. 2.2 with complex exponentials in place of cosines):
+ *     ybar_i(x) = Re sum_{k in Gamma} alpha_{i,k} phi_k(x).
+ * One Picard iteration recomputes every row i from the previous iterate at
+ * once; each row is the Monte-Carlo projection of Algorithm 1 (Sec. 2.3):
+ *     alpha_{i,k} = (1/M) sum_m S_i^m conj(phi_k(X_i^{i,m})),  X_i^{i,m} ~ nu,
+ *     S_i = g(X_N) + sum_{j=i}^{N-1} f(t_j, X_j, T_L(ybar_{j+1}(X_{j+1}))) dt,
+ * with no linear solve.
+ *
+ * Conventions for every call:
+ *  - Every call returns a qr_status and never aborts or exits. Errors found
+ *    on the device (a bounded wait that ran out, non-finite responses) are
+ *    recorded in the context and returned by the call that launched the
+ *    work; qr_last_error() gives a text.
+ *  - The caller owns every array it passes. The context owns its device
+ *    buffers (allocated with cudaMallocAsync on the context's stream at
+ *    qr_init, freed by qr_destroy).
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - Host arrays are plain C arrays; "device" arrays are CUDA device
+ *    pointers of the current device.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with
+ *   key = (seed & 0xffffffff, seed >> 32),
+ *   counter = (m, c, j, (instance << 20) | (tag << 16) | i),
+ * tag 0 = start point (j = 0xffffffff), 1 = Brownian increment of step j,
+ * 2 = test point. A uniform is u = (2n+1) 2^-53 with the 52-bit integer
+ * n = (w0 << 20) ^ (w1 >> 12) of two words; call c of a path gives
+ * coordinates 2c and 2c+1 (start: words (0,1) and (2,3); increments: one
+ * Box-Muller pair z = sqrt(-2 ln u_a) (cos 2 pi u_b, sin 2 pi u_b)).
+ */
+#ifndef QR_H
+#define QR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qr_ctx qr_ctx;
+
+typedef enum {
+    QR_OK = 0,
+    QR_EINVAL = 1,      /* bad argument; nothing was launched */
+    QR_ENOMEM = 2,      /* device or host allocation failed */
+    QR_ECUDA = 3,       /* a CUDA runtime call failed (text in qr_last_error) */
+    QR_ETIMEOUT = 4,    /* a bounded device wait ran out; results are invalid */
+    QR_ENONFINITE = 5,  /* some responses were NaN/Inf; results are invalid */
+    QR_ENOTIMPL = 6     /* combination not supported by this build */
+} qr_status;
+
+/* sampling density nu of the start points (Sec. 2.1.2), same 1-D marginal
+ * in every coordinate */
+enum {
+    QR_NU_LOMAX = 0,    /* (mu/2)(1+|x|)^-(mu+1)                  mu > 0 */
+    QR_NU_STUDENT2 = 1, /* 0.5 (1+x^2)^-3/2  (Student mu = 2, Sec. 5) */
+    QR_NU_CAUCHY = 2    /* 1/(pi (1+x^2))    (Student mu = 1, Sec. 5) */
+};
+typedef struct {
+    int kind;
+    double mu;          /* used by QR_NU_LOMAX */
+} qr_nu;
+
+/* index sets of Z^d, symmetric under k -> -k (Sec. 2.4.2 lists their N^d
+ * counterparts). Canonical order: lexicographic, k_1 most significant. */
+enum {
+    QR_G_LINF = 0,      /* max_l |k_l| <= n */
+    QR_G_L1 = 1,        /* sum_l |k_l| <= n */
+    QR_G_HYP = 2        /* prod_l max(|k_l|,1) <= n */
+};
+typedef struct {
+    int kind;
+    int n;
+} qr_gamma;
+
+/* driver f(t, x, y) and terminal condition g(x) */
+enum {
+    QR_F_ZERO = 0,        /* f = 0                                  params: none */
+    QR_F_LINEAR = 1,      /* f = lambda y                           params: {lambda} */
+    QR_F_CUBIC_MANUF = 2, /* f = -y^3 + r(t,x), r = (a + |sigma^T s|^2/2) u + u^3,
+                             u = e^{a(T-t)} cos(s.x)                params: {a, s_1..s_d} */
+    QR_F_PAPER_MIN = 3    /* Sec. 5: min(1, [y-kappa-1-sin(lambda sum x) e^{lambda^2 d (t-T)/2}]^2)
+                                                                    params: {kappa, lambda} */
+};
+enum {
+    QR_GT_COS = 0,        /* g = cos(s.x)                           params: {s_1..s_d} */
+    QR_GT_TRIGPOLY = 1,   /* g = Re sum_{k in Gamma} c_k phi_k(x)   params: 2|Gamma| doubles
+                             (re, im interleaved, canonical order, c_{-k} = conj(c_k)) */
+    QR_GT_PAPER_SIN = 2   /* Sec. 5: g = 1 + kappa + sin(lambda sum x)  params: {kappa, lambda} */
+};
+typedef struct {
+    int kind;
+    const double* params; /* host array, copied by qr_init */
+    int n_params;
+} qr_fn;
+
+enum { QR_FP64 = 0, QR_FP32 = 1 };
+enum { QR_U_PHILOX = 0, QR_U_LATTICE = 1 };
+enum { QR_HOST = 0, QR_DEVICE = 1 };
+
+typedef struct {
+    long long M;              /* paths per time index, 1 <= M <= 2^32 */
+    unsigned long long seed;  /* Philox key */
+    int precision;            /* QR_FP64 (plain form) or QR_FP32 (precision form:
+                                 FP32 path/basis math, FP64 cross-block sums and alpha) */
+    double clamp_L;           /* truncation T_L (eq. TL:2) at the constant level L; <= 0: off */
+    void* stream;             /* cudaStream_t for all work; NULL: the context makes its own */
+    int uniform_source;       /* QR_U_PHILOX, or QR_U_LATTICE: start uniforms on the centred
+                                 lattice u_l = (digit_l(m) + 1/2)/lattice_n, M = lattice_n^d
+                                 (test hook: lattice sums integrate trigonometric
+                                 polynomials exactly) */
+    int lattice_n;
+    int instance;             /* Philox counter field, 0 <= instance < 4096 */
+} qr_opts;
+
+/* Creates a context: validates the problem, enumerates Gamma, allocates the
+ * device state and sets alpha = 0 (ybar == 0 start).
+ *   d in [1, 8]; N in [1, 256]; T > 0; b: d doubles (host); sigma: d*d doubles,
+ *   row-major (host), X_{j+1} = X_j + b dt + sigma sqrt(dt) Z; every |k_l| <= 7.
+ *   opts may be NULL: M = 2^14, seed 1, QR_FP64, no truncation. */
+qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const qr_gamma* gamma,
+                  const double* b, const double* sigma, const qr_fn* f, const qr_fn* g,
+                  const qr_opts* opts);
+
+/* Runs n_iter Jacobi-Picard iterations: every row i in [0, N) is recomputed
+ * from the previous iterate (Algorithm 1's projection for all i at once).
+ * residual_out (host, nullable): max_{i,k} |alpha^(q) - alpha^(q-1)| of the
+ * last iteration. Blocks until the work is done. */
+qr_status qr_picard_step(qr_ctx* ctx, int n_iter, double* residual_out);
+
+/* Algorithm 1 as printed: backward sweep i = N-1 .. 0, each row projected
+ * with the rows above it already final. Equals N Picard iterations. */
+qr_status qr_backward_sweep(qr_ctx* ctx);
+
+/* ybar_i at n points: y[p] = Re sum_k alpha_{i,k} phi_k(x_p) for 0 <= i < N,
+ * g(x_p) for i = N. x: n*d doubles (row per point), y: n doubles; both host
+ * (ptr_kind = QR_HOST) or both device (QR_DEVICE). Blocks until done. */
+qr_status qr_eval(qr_ctx* ctx, int i, const double* x, long long n, double* y_out, int ptr_kind);
+
+/* |Gamma| and the list of k (|Gamma|*d ints, host, canonical order). */
+qr_status qr_gamma_size(const qr_ctx* ctx, int* n_gamma);
+qr_status qr_gamma_list(const qr_ctx* ctx, int* k_out);
+
+/* alpha: N*|Gamma| complex as interleaved (re, im) doubles, row i = time index
+ * i, canonical Gamma order (host). set_coefs expects conjugate symmetry
+ * alpha_{-k} = conj(alpha_k) and reads only k = 0 and the half k > 0. */
+qr_status qr_get_coefs(const qr_ctx* ctx, double* alpha_out);
+qr_status qr_set_coefs(qr_ctx* ctx, const double* alpha_in);
+
+/* Responses S_i^m (m = 0..M-1) of row i from the last iteration (host). */
+qr_status qr_get_responses(const qr_ctx* ctx, int i, double* S_out);
+
+typedef struct {
+    long long iterations;       /* Picard iterations (or sweeps) run */
+    long long clamp_hits;       /* truncations T_L applied, all iterations */
+    long long nonfinite;        /* non-finite responses, all iterations */
+    double ms_paths;            /* device time of the path-and-series kernel (events) */
+    double ms_project;          /* device time of the projection kernel */
+    double ms_reduce;           /* device time of the cross-block reduction */
+    long long launches_paths, launches_project, launches_reduce;
+} qr_stats_t;
+/* Kernel timing is recorded only when enabled (events cost a little). */
+qr_status qr_set_profiling(qr_ctx* ctx, int on);
+qr_status qr_get_stats(const qr_ctx* ctx, qr_stats_t* out);
+
+const char* qr_last_error(const qr_ctx* ctx);
+const char* qr_status_string(qr_status s);
+void qr_destroy(qr_ctx* ctx);
+
+/* ---- test hooks (no context) ------------------------------------------ */
+
+/* Philox4x32-10 on the device: ctr_key is n rows of 6 words (ctr0..3, key0,1),
+ * out is n rows of 4 words (host arrays). */
+qr_status qr_philox_words(const uint32_t* ctr_key, long long n, uint32_t* out);
+
+/* The device sampler of paths m0 .. m0+n-1 of row i: d start uniforms
+ * (u_out, n*d, exact doubles), d start points F_nu^{-1}(u) (x_out, n*d)
+ * and the d normals of Euler step j (z_out, n*d), computed in `precision`
+ * (QR_FP32 results are widened to double). Host arrays; any may be NULL. */
+qr_status qr_sample(int d, const qr_nu* nu, unsigned long long seed, int instance, int i,
+                    long long m0, long long n, int j, int precision, double* u_out,
+                    double* x_out, double* z_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,133 @@
+"""ctypes binding of libqrmc (include/qr.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module converts numpy
+arrays and torch tensors to pointers and raises on error statuses. There is
+no CPU fallback: if the library is missing or cannot load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqrmc.so")
+
+QR_OK, QR_EINVAL, QR_ENOMEM, QR_ECUDA, QR_ETIMEOUT, QR_ENONFINITE, QR_ENOTIMPL = range(7)
+QR_NU_LOMAX, QR_NU_STUDENT2, QR_NU_CAUCHY = range(3)
+QR_G_LINF, QR_G_L1, QR_G_HYP = range(3)
+QR_F_ZERO, QR_F_LINEAR, QR_F_CUBIC_MANUF, QR_F_PAPER_MIN = range(4)
+QR_GT_COS, QR_GT_TRIGPOLY, QR_GT_PAPER_SIN = range(3)
+QR_FP64, QR_FP32 = 0, 1
+QR_U_PHILOX, QR_U_LATTICE = 0, 1
+QR_HOST, QR_DEVICE = 0, 1
+
+# every symbol declared in include/qr.h
+EXPORTS = [
+    "qr_init", "qr_picard_step", "qr_backward_sweep", "qr_eval", "qr_gamma_size", "qr_gamma_list",
+    "qr_get_coefs", "qr_set_coefs", "qr_get_responses", "qr_set_profiling", "qr_get_stats",
+    "qr_last_error", "qr_status_string", "qr_destroy", "qr_philox_words", "qr_sample",
+]
+
+
+class QrNu(C.Structure):
+    _fields_ = [("kind", C.c_int), ("mu", C.c_double)]
+
+
+class QrGamma(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n", C.c_int)]
+
+
+class QrFn(C.Structure):
+    _fields_ = [("kind", C.c_int), ("params", C.POINTER(C.c_double)), ("n_params", C.c_int)]
+
+
+class QrOpts(C.Structure):
+    _fields_ = [
+        ("M", C.c_longlong),
+        ("seed", C.c_ulonglong),
+        ("precision", C.c_int),
+        ("clamp_L", C.c_double),
+        ("stream", C.c_void_p),
+        ("uniform_source", C.c_int),
+        ("lattice_n", C.c_int),
+        ("instance", C.c_int),
+    ]
+
+
+class QrStats(C.Structure):
+    _fields_ = [
+        ("iterations", C.c_longlong),
+        ("clamp_hits", C.c_longlong),
+        ("nonfinite", C.c_longlong),
+        ("ms_paths", C.c_double),
+        ("ms_project", C.c_double),
+        ("ms_reduce", C.c_double),
+        ("launches_paths", C.c_longlong),
+        ("launches_project", C.c_longlong),
+        ("launches_reduce", C.c_longlong),
+    ]
+
+
+class QrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("qr status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libqrmc.so (built in-tree by paper_2407_21084_b300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError("libqrmc.so is not built (run python -m paper_2407_21084_b300.build)")
+    L = C.CDLL(p)
+    dp = C.POINTER(C.c_double)
+    vp = C.c_void_p
+    L.qr_init.restype = C.c_int
+    L.qr_init.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_double, C.POINTER(QrNu), C.POINTER(QrGamma), dp, dp,
+                          C.POINTER(QrFn), C.POINTER(QrFn), C.POINTER(QrOpts)]
+    L.qr_picard_step.restype = C.c_int
+    L.qr_picard_step.argtypes = [vp, C.c_int, dp]
+    L.qr_backward_sweep.restype = C.c_int
+    L.qr_backward_sweep.argtypes = [vp]
+    L.qr_eval.restype = C.c_int
+    L.qr_eval.argtypes = [vp, C.c_int, vp, C.c_longlong, vp, C.c_int]
+    L.qr_gamma_size.restype = C.c_int
+    L.qr_gamma_size.argtypes = [vp, C.POINTER(C.c_int)]
+    L.qr_gamma_list.restype = C.c_int
+    L.qr_gamma_list.argtypes = [vp, C.POINTER(C.c_int)]
+    L.qr_get_coefs.restype = C.c_int
+    L.qr_get_coefs.argtypes = [vp, dp]
+    L.qr_set_coefs.restype = C.c_int
+    L.qr_set_coefs.argtypes = [vp, dp]
+    L.qr_get_responses.restype = C.c_int
+    L.qr_get_responses.argtypes = [vp, C.c_int, dp]
+    L.qr_set_profiling.restype = C.c_int
+    L.qr_set_profiling.argtypes = [vp, C.c_int]
+    L.qr_get_stats.restype = C.c_int
+    L.qr_get_stats.argtypes = [vp, C.POINTER(QrStats)]
+    L.qr_last_error.restype = C.c_char_p
+    L.qr_last_error.argtypes = [vp]
+    L.qr_status_string.restype = C.c_char_p
+    L.qr_status_string.argtypes = [C.c_int]
+    L.qr_destroy.restype = None
+    L.qr_destroy.argtypes = [vp]
+    L.qr_philox_words.restype = C.c_int
+    L.qr_philox_words.argtypes = [C.POINTER(C.c_uint32), C.c_longlong, C.POINTER(C.c_uint32)]
+    L.qr_sample.restype = C.c_int
+    L.qr_sample.argtypes = [C.c_int, C.POINTER(QrNu), C.c_ulonglong, C.c_int, C.c_int, C.c_longlong, C.c_longlong,
+                            C.c_int, C.c_int, dp, dp, dp]
+    _lib = L
+    return L
+
+
+def check(status: int, ctx=None):
+    if status != QR_OK:
+        L = load()
+        msg = L.qr_last_error(ctx).decode() if ctx else L.qr_status_string(status).decode()
+        raise QrError(status, msg or L.qr_status_string(status).decode())

@@ -1,0 +1,592 @@
+// qr_api.cu -- host side of libqrmc: argument checking, the index set Gamma,
+// the coefficient table, device state and the C-ABI of include/qr.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qr_internal.h"
+
+using namespace qr;
+
+struct qr_ctx {
+    int d = 0, N = 0, prec = QR_FP64;
+    int nG = 0, nGp = 0, zero_idx = 0, kmax = 0;
+    std::vector<int> k;  // nG * d, canonical order
+    QrParams P{};
+    bool trig_g = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    long long row_stride = 0;  // elements of the packed coefficient rows
+    size_t elem = 0;           // bytes of one packed coefficient
+    GEntry* d_tab = nullptr;
+    uint8_t* d_first = nullptr;
+    double2* d_alpha = nullptr;  // (N+1) x nG, row N = coefficients of a polynomial g
+    void* d_packed = nullptr;    // (N+1) x row_stride
+    void* d_S = nullptr;         // N x M responses (float or double)
+    double2* d_partial = nullptr;
+    unsigned long long* d_counters = nullptr;
+    unsigned* d_status = nullptr;
+    unsigned long long* h_counters = nullptr;  // pinned
+    bool profiling = false;
+    cudaEvent_t ev[8] = {};
+    qr_stats_t stats{};
+    std::string err;
+};
+
+namespace {
+
+qr_status fail(qr_ctx* c, qr_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+qr_status cuda_fail(qr_ctx* c, cudaError_t e, const char* where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (c) c->err = m;
+    return QR_ECUDA;
+}
+
+#define QR_CU(ctx, call)                                    \
+    do {                                                    \
+        cudaError_t _e = (call);                            \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
+    } while (0)
+
+// Gamma of Z^d in canonical (lexicographic) order.
+void enumerate_gamma(int kind, int d, int n, std::vector<int>& out)
+{
+    std::vector<int> k(d, 0);
+    std::function<void(int, long long, long long)> rec = [&](int l, long long s, long long prod) {
+        for (int v = -n; v <= n; ++v) {
+            const long long a = v < 0 ? -v : v;
+            long long s2 = s, p2 = prod;
+            if (kind == QR_G_LINF) {
+                if (a > n) continue;
+            } else if (kind == QR_G_L1) {
+                s2 = s + a;
+                if (s2 > n) continue;
+            } else {
+                p2 = prod * (a > 1 ? a : 1);
+                if (p2 > n) continue;
+            }
+            k[l] = v;
+            if (l + 1 == d)
+                out.insert(out.end(), k.begin(), k.end());
+            else
+                rec(l + 1, s2, p2);
+        }
+    };
+    rec(0, 0, 1);
+}
+
+template <typename T>
+qr_status dalloc(qr_ctx* c, T** p, size_t bytes)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, bytes < 16 ? 16 : bytes, c->stream);
+    if (e != cudaSuccess) return fail(c, QR_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+    *p = static_cast<T*>(q);
+    return QR_OK;
+}
+
+void release(qr_ctx* c)
+{
+    if (!c) return;
+    if (c->stream || c->own_stream) {
+        void* ptrs[] = {c->d_tab, c->d_first, c->d_alpha, c->d_packed, c->d_S, c->d_partial, c->d_counters, c->d_status};
+        for (void* p : ptrs)
+            if (p) cudaFreeAsync(p, c->stream);
+        cudaStreamSynchronize(c->stream);
+    }
+    if (c->h_counters) cudaFreeHost(c->h_counters);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+qr_status check_device_status(qr_ctx* c)
+{
+    QR_CU(c, cudaMemcpyAsync(c->h_counters, c->d_counters, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost,
+                             c->stream));
+    unsigned st = 0;
+    QR_CU(c, cudaMemcpyAsync(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    QR_CU(c, cudaStreamSynchronize(c->stream));
+    c->stats.clamp_hits = (long long)c->h_counters[CNT_CLAMP];
+    c->stats.nonfinite = (long long)c->h_counters[CNT_NONFINITE];
+    if (st & ST_TIMEOUT) return fail(c, QR_ETIMEOUT, "a bounded wait for a bulk copy ran out on the device");
+    return QR_OK;
+}
+
+struct Timer {
+    qr_ctx* c;
+    int slot;
+    Timer(qr_ctx* c_, int s) : c(c_), slot(s)
+    {
+        if (c->profiling) cudaEventRecord(c->ev[2 * slot], c->stream);
+    }
+    ~Timer()
+    {
+        if (c->profiling) cudaEventRecord(c->ev[2 * slot + 1], c->stream);
+    }
+};
+
+void harvest(qr_ctx* c, int slot)
+{
+    if (!c->profiling) return;
+    float ms = 0.f;
+    if (cudaEventSynchronize(c->ev[2 * slot + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, c->ev[2 * slot], c->ev[2 * slot + 1]) == cudaSuccess) {
+        if (slot == 0) c->stats.ms_paths += ms, c->stats.launches_paths++;
+        if (slot == 1) c->stats.ms_project += ms, c->stats.launches_project++;
+        if (slot == 2) c->stats.ms_reduce += ms, c->stats.launches_reduce++;
+    }
+}
+
+// one projection of rows [i_lo, i_hi) from the current packed coefficients
+qr_status run_rows(qr_ctx* c, int i_lo, int i_hi)
+{
+    QR_CU(c, cudaMemsetAsync(c->d_counters + CNT_RESID, 0, sizeof(unsigned long long), c->stream));
+    {
+        Timer t(c, 0);
+        cudaError_t e = launch_paths(c->prec, c->P, c->d_tab, c->d_first, c->d_packed, c->row_stride, c->d_S, i_lo,
+                                     i_hi, c->d_counters, c->d_status, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "path-and-series kernel");
+    }
+    harvest(c, 0);
+    {
+        Timer t(c, 1);
+        cudaError_t e = launch_project(c->prec, c->P, c->d_tab, c->d_first, c->d_S, c->d_partial, i_lo, i_hi, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "projection kernel");
+    }
+    harvest(c, 1);
+    {
+        Timer t(c, 2);
+        cudaError_t e = launch_reduce(c->prec, c->P, c->d_partial, c->d_alpha, c->nG, c->zero_idx, c->d_packed,
+                                      c->row_stride, i_lo, i_hi, c->d_counters, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "reduction kernel");
+    }
+    harvest(c, 2);
+    return QR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qr_status_string(qr_status s)
+{
+    switch (s) {
+    case QR_OK: return "ok";
+    case QR_EINVAL: return "invalid argument";
+    case QR_ENOMEM: return "out of memory";
+    case QR_ECUDA: return "CUDA error";
+    case QR_ETIMEOUT: return "device wait timed out";
+    case QR_ENONFINITE: return "non-finite responses";
+    case QR_ENOTIMPL: return "not implemented";
+    }
+    return "unknown status";
+}
+
+const char* qr_last_error(const qr_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const qr_gamma* gamma, const double* b,
+                  const double* sigma, const qr_fn* f, const qr_fn* g, const qr_opts* opts)
+{
+    if (!out) return QR_EINVAL;
+    *out = nullptr;
+    qr_ctx* c = new (std::nothrow) qr_ctx();
+    if (!c) return QR_ENOMEM;
+    auto bail = [&](qr_status s, const std::string& m) {
+        // keep the context so that the caller can read the message, but no
+        // device state: the caller must still qr_destroy it
+        c->err = m;
+        *out = c;
+        return s;
+    };
+    if (d < 1 || d > kDMax) return bail(QR_EINVAL, "d must be in [1, 8]");
+    if (N < 1 || N > kNMax) return bail(QR_EINVAL, "N must be in [1, 256]");
+    if (!(T > 0.0) || !std::isfinite(T)) return bail(QR_EINVAL, "T must be positive");
+    if (!nu || !gamma || !b || !sigma || !f || !g) return bail(QR_EINVAL, "null argument");
+    if (nu->kind < QR_NU_LOMAX || nu->kind > QR_NU_CAUCHY) return bail(QR_EINVAL, "unknown nu kind");
+    if (nu->kind == QR_NU_LOMAX && !(nu->mu > 0.0)) return bail(QR_EINVAL, "nu: mu must be positive");
+    if (gamma->kind < QR_G_LINF || gamma->kind > QR_G_HYP || gamma->n < (gamma->kind == QR_G_HYP ? 1 : 0))
+        return bail(QR_EINVAL, "bad index set");
+    qr_opts o{};
+    o.M = 1 << 14;
+    o.seed = 1;
+    o.precision = QR_FP64;
+    if (opts) o = *opts;
+    if (o.M < 1 || o.M > (1ll << 32)) return bail(QR_EINVAL, "M must be in [1, 2^32]");
+    if (o.precision != QR_FP32 && o.precision != QR_FP64) return bail(QR_EINVAL, "unknown precision");
+    if (o.instance < 0 || o.instance >= 4096) return bail(QR_EINVAL, "instance must be in [0, 4096)");
+    if (o.uniform_source == QR_U_LATTICE) {
+        if (o.lattice_n < 1) return bail(QR_EINVAL, "lattice_n must be positive");
+        long long L = 1;
+        for (int l = 0; l < d; ++l) L *= o.lattice_n;
+        if (L != o.M) return bail(QR_EINVAL, "lattice start points need M = lattice_n^d");
+    } else if (o.uniform_source != QR_U_PHILOX) {
+        return bail(QR_EINVAL, "unknown uniform source");
+    }
+    c->d = d;
+    c->N = N;
+    c->prec = o.precision;
+
+    // index set and coefficient table
+    enumerate_gamma(gamma->kind, d, gamma->n, c->k);
+    c->nG = (int)(c->k.size() / d);
+    c->zero_idx = (c->nG - 1) / 2;
+    for (int l = 0; l < d; ++l)
+        if (c->k[(size_t)c->zero_idx * d + l] != 0) return bail(QR_EINVAL, "index set is not symmetric");
+    for (int v : c->k) c->kmax = std::max(c->kmax, v < 0 ? -v : v);
+    if (c->kmax > kKMax) return bail(QR_ENOTIMPL, "|k_l| <= 7 is required");
+    c->nGp = c->nG - c->zero_idx;
+    std::vector<GEntry> tab(c->nGp);
+    std::vector<uint8_t> first(c->nGp, 0);
+    for (int e = 0; e < c->nGp; ++e) {
+        std::memset(tab[e].k, 0, sizeof(tab[e].k));
+        for (int l = 0; l < d; ++l) tab[e].k[l] = (signed char)c->k[(size_t)(c->zero_idx + e) * d + l];
+        if (e > 0) {
+            int f0 = 0;
+            while (f0 < d && tab[e].k[f0] == tab[e - 1].k[f0]) ++f0;
+            first[e] = (uint8_t)f0;
+        }
+    }
+
+    // problem parameters
+    QrParams& P = c->P;
+    P.d = d;
+    P.N = N;
+    P.nGp = c->nGp;
+    P.K1 = c->kmax + 1;
+    P.M = o.M;
+    P.nu_kind = nu->kind;
+    P.mu = nu->kind == QR_NU_LOMAX ? nu->mu : (nu->kind == QR_NU_STUDENT2 ? 2.0 : 1.0);
+    P.inv_mu = 1.0 / P.mu;
+    P.mu_is3 = nu->kind == QR_NU_LOMAX && nu->mu == 3.0;
+    P.T = T;
+    P.dt = T / N;
+    P.sqdt = std::sqrt(P.dt);
+    P.sig_diag = 1;
+    for (int l = 0; l < d; ++l) {
+        P.b[l] = b[l];
+        for (int cc = 0; cc < d; ++cc) {
+            P.sig[l * d + cc] = sigma[l * d + cc];
+            if (l != cc && sigma[l * d + cc] != 0.0) P.sig_diag = 0;
+        }
+    }
+    P.f_kind = f->kind;
+    switch (f->kind) {
+    case QR_F_ZERO:
+        break;
+    case QR_F_LINEAR:
+        if (!f->params || f->n_params < 1) return bail(QR_EINVAL, "linear driver needs {lambda}");
+        P.f_lam = f->params[0];
+        break;
+    case QR_F_CUBIC_MANUF: {
+        if (!f->params || f->n_params < 1 + d) return bail(QR_EINVAL, "cubic driver needs {a, s_1..s_d}");
+        const double a = f->params[0];
+        double st2 = 0.0;
+        for (int cc = 0; cc < d; ++cc) {
+            double v = 0.0;
+            for (int l = 0; l < d; ++l) v += sigma[l * d + cc] * f->params[1 + l];
+            st2 += v * v;
+        }
+        for (int l = 0; l < d; ++l) P.f_s[l] = f->params[1 + l];
+        P.f_c = a + 0.5 * st2;
+        for (int j = 0; j < N; ++j) P.fexp[j] = std::exp(a * (T - j * P.dt));
+        break;
+    }
+    case QR_F_PAPER_MIN:
+        if (!f->params || f->n_params < 2) return bail(QR_EINVAL, "paper driver needs {kappa, lambda}");
+        P.f_kap = f->params[0];
+        P.f_lam = f->params[1];
+        for (int j = 0; j < N; ++j) P.fexp[j] = std::exp(P.f_lam * P.f_lam * d * (j * P.dt - T) / 2.0);
+        break;
+    default:
+        return bail(QR_EINVAL, "unknown driver");
+    }
+    P.g_kind = g->kind;
+    if (g->kind == QR_GT_COS) {
+        if (!g->params || g->n_params < d) return bail(QR_EINVAL, "cos terminal needs {s_1..s_d}");
+        for (int l = 0; l < d; ++l) P.g_s[l] = g->params[l];
+    } else if (g->kind == QR_GT_PAPER_SIN) {
+        if (!g->params || g->n_params < 2) return bail(QR_EINVAL, "paper terminal needs {kappa, lambda}");
+        P.g_kap = g->params[0];
+        P.g_lam = g->params[1];
+    } else if (g->kind == QR_GT_TRIGPOLY) {
+        if (!g->params || g->n_params < 2 * c->nG) return bail(QR_EINVAL, "polynomial terminal needs 2|Gamma| values");
+        c->trig_g = true;
+    } else {
+        return bail(QR_EINVAL, "unknown terminal condition");
+    }
+    P.key0 = (uint32_t)(o.seed & 0xffffffffull);
+    P.key1 = (uint32_t)(o.seed >> 32);
+    P.instance = o.instance;
+    P.clamp_L = o.clamp_L;
+    P.lattice_n = o.uniform_source == QR_U_LATTICE ? o.lattice_n : 0;
+    const int BS = c->prec == QR_FP32 ? 256 : 128;
+    const long long per = (o.M + 256ll * BS - 1) / (256ll * BS);
+    P.chunk = (int)(BS * std::max(1ll, per));
+    P.n_chunks = (int)((o.M + P.chunk - 1) / P.chunk);
+
+    // device state
+    QR_CU(c, cudaGetDevice(&c->device));
+    if (o.stream) {
+        c->stream = static_cast<cudaStream_t>(o.stream);
+    } else {
+        QR_CU(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    c->elem = c->prec == QR_FP32 ? sizeof(float2) : sizeof(double2);
+    c->row_stride = c->prec == QR_FP32 ? ((c->nGp + 1) & ~1) : c->nGp;  // rows of 16-byte multiples
+    qr_status s;
+    if ((s = dalloc(c, &c->d_tab, sizeof(GEntry) * c->nGp)) != QR_OK) return bail(s, c->err);
+    if ((s = dalloc(c, &c->d_first, c->nGp)) != QR_OK) return bail(s, c->err);
+    if ((s = dalloc(c, &c->d_alpha, sizeof(double2) * (size_t)(N + 1) * c->nG)) != QR_OK) return bail(s, c->err);
+    if ((s = dalloc(c, &c->d_packed, c->elem * (size_t)(N + 1) * c->row_stride)) != QR_OK) return bail(s, c->err);
+    if ((s = dalloc(c, &c->d_S, (c->prec == QR_FP32 ? 4 : 8) * (size_t)N * (size_t)o.M)) != QR_OK)
+        return bail(s, c->err);
+    if ((s = dalloc(c, &c->d_partial, sizeof(double2) * (size_t)N * P.n_chunks * c->nGp)) != QR_OK)
+        return bail(s, c->err);
+    if ((s = dalloc(c, &c->d_counters, sizeof(unsigned long long) * CNT_N)) != QR_OK) return bail(s, c->err);
+    if ((s = dalloc(c, &c->d_status, sizeof(unsigned))) != QR_OK) return bail(s, c->err);
+    if (cudaMallocHost(&c->h_counters, sizeof(unsigned long long) * CNT_N) != cudaSuccess)
+        return bail(QR_ENOMEM, "pinned host allocation failed");
+    for (auto& e : c->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return bail(QR_ECUDA, "event creation failed");
+
+    auto cu = [&](cudaError_t e, const char* w) { return e == cudaSuccess ? QR_OK : cuda_fail(c, e, w); };
+    if ((s = cu(cudaMemcpyAsync(c->d_tab, tab.data(), sizeof(GEntry) * c->nGp, cudaMemcpyHostToDevice, c->stream),
+                "copy table")) != QR_OK ||
+        (s = cu(cudaMemcpyAsync(c->d_first, first.data(), c->nGp, cudaMemcpyHostToDevice, c->stream), "copy table")) !=
+            QR_OK ||
+        (s = cu(cudaMemsetAsync(c->d_alpha, 0, sizeof(double2) * (size_t)(N + 1) * c->nG, c->stream), "zero alpha")) !=
+            QR_OK ||
+        (s = cu(cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * CNT_N, c->stream), "zero counters")) !=
+            QR_OK ||
+        (s = cu(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream), "zero status")) != QR_OK)
+        return bail(s, c->err);
+    if (c->trig_g) {
+        if ((s = cu(cudaMemcpyAsync(c->d_alpha + (size_t)N * c->nG, g->params, sizeof(double2) * c->nG,
+                                    cudaMemcpyHostToDevice, c->stream),
+                    "copy terminal polynomial")) != QR_OK)
+            return bail(s, c->err);
+    }
+    if ((s = cu(launch_pack(c->prec, P, c->d_alpha, c->nG, c->zero_idx, c->d_packed, c->row_stride, N + 1, c->stream),
+                "pack")) != QR_OK)
+        return bail(s, c->err);
+    if ((s = cu(cudaStreamSynchronize(c->stream), "init sync")) != QR_OK) return bail(s, c->err);
+    *out = c;
+    return QR_OK;
+}
+
+void qr_destroy(qr_ctx* ctx)
+{
+    if (!ctx) return;
+    release(ctx);
+    delete ctx;
+}
+
+static bool ready(const qr_ctx* c) { return c && c->d_packed; }
+
+qr_status qr_picard_step(qr_ctx* ctx, int n_iter, double* residual_out)
+{
+    if (!ready(ctx)) return QR_EINVAL;
+    if (n_iter < 0) return fail(ctx, QR_EINVAL, "n_iter must be >= 0");
+    for (int q = 0; q < n_iter; ++q) {
+        qr_status s = run_rows(ctx, 0, ctx->N);
+        if (s != QR_OK) return s;
+        ctx->stats.iterations++;
+    }
+    const long long nonfinite_before = ctx->stats.nonfinite;
+    qr_status s = check_device_status(ctx);
+    if (s != QR_OK) return s;
+    if (residual_out) {
+        unsigned long long bits = ctx->h_counters[CNT_RESID];
+        double r;
+        std::memcpy(&r, &bits, sizeof r);
+        *residual_out = n_iter > 0 ? r : 0.0;
+    }
+    if (ctx->stats.nonfinite > nonfinite_before) return fail(ctx, QR_ENONFINITE, "non-finite responses");
+    return QR_OK;
+}
+
+qr_status qr_backward_sweep(qr_ctx* ctx)
+{
+    if (!ready(ctx)) return QR_EINVAL;
+    for (int i = ctx->N - 1; i >= 0; --i) {
+        qr_status s = run_rows(ctx, i, i + 1);
+        if (s != QR_OK) return s;
+    }
+    ctx->stats.iterations++;
+    const long long nonfinite_before = ctx->stats.nonfinite;
+    qr_status s = check_device_status(ctx);
+    if (s != QR_OK) return s;
+    if (ctx->stats.nonfinite > nonfinite_before) return fail(ctx, QR_ENONFINITE, "non-finite responses");
+    return QR_OK;
+}
+
+qr_status qr_eval(qr_ctx* ctx, int i, const double* x, long long n, double* y_out, int ptr_kind)
+{
+    if (!ready(ctx)) return QR_EINVAL;
+    if (i < 0 || i > ctx->N || n < 0 || (n > 0 && (!x || !y_out)) || (ptr_kind != QR_HOST && ptr_kind != QR_DEVICE))
+        return fail(ctx, QR_EINVAL, "qr_eval: bad arguments");
+    if (n == 0) return QR_OK;
+    const double* dx = x;
+    double* dy = y_out;
+    double* tmp = nullptr;
+    if (ptr_kind == QR_HOST) {
+        QR_CU(ctx, cudaMallocAsync(&tmp, sizeof(double) * (size_t)n * (ctx->d + 1), ctx->stream));
+        QR_CU(ctx, cudaMemcpyAsync(tmp, x, sizeof(double) * (size_t)n * ctx->d, cudaMemcpyHostToDevice, ctx->stream));
+        dx = tmp;
+        dy = tmp + (size_t)n * ctx->d;
+    }
+    const int use_g = (i == ctx->N && !ctx->trig_g) ? 1 : 0;
+    const void* row = static_cast<const char*>(ctx->d_packed) + ctx->elem * (size_t)i * ctx->row_stride;
+    cudaError_t e = launch_eval(ctx->prec, ctx->P, ctx->d_tab, ctx->d_first, row, dx, n, dy, use_g, ctx->stream);
+    if (e != cudaSuccess) {
+        if (tmp) cudaFreeAsync(tmp, ctx->stream);
+        return cuda_fail(ctx, e, "evaluation kernel");
+    }
+    if (ptr_kind == QR_HOST) {
+        QR_CU(ctx, cudaMemcpyAsync(y_out, dy, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+        QR_CU(ctx, cudaFreeAsync(tmp, ctx->stream));
+    }
+    QR_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return QR_OK;
+}
+
+qr_status qr_gamma_size(const qr_ctx* ctx, int* n_gamma)
+{
+    if (!ready(ctx) || !n_gamma) return QR_EINVAL;
+    *n_gamma = ctx->nG;
+    return QR_OK;
+}
+
+qr_status qr_gamma_list(const qr_ctx* ctx, int* k_out)
+{
+    if (!ready(ctx) || !k_out) return QR_EINVAL;
+    std::memcpy(k_out, ctx->k.data(), sizeof(int) * ctx->k.size());
+    return QR_OK;
+}
+
+qr_status qr_get_coefs(const qr_ctx* ctx, double* alpha_out)
+{
+    if (!ready(ctx) || !alpha_out) return QR_EINVAL;
+    qr_ctx* c = const_cast<qr_ctx*>(ctx);
+    QR_CU(c, cudaMemcpyAsync(alpha_out, ctx->d_alpha, sizeof(double2) * (size_t)ctx->N * ctx->nG, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    QR_CU(c, cudaStreamSynchronize(ctx->stream));
+    return QR_OK;
+}
+
+qr_status qr_set_coefs(qr_ctx* ctx, const double* alpha_in)
+{
+    if (!ready(ctx) || !alpha_in) return QR_EINVAL;
+    for (long long t = 0; t < 2ll * ctx->N * ctx->nG; ++t)
+        if (!std::isfinite(alpha_in[t])) return fail(ctx, QR_EINVAL, "qr_set_coefs: non-finite coefficient");
+    QR_CU(ctx, cudaMemcpyAsync(ctx->d_alpha, alpha_in, sizeof(double2) * (size_t)ctx->N * ctx->nG,
+                               cudaMemcpyHostToDevice, ctx->stream));
+    QR_CU(ctx, launch_pack(ctx->prec, ctx->P, ctx->d_alpha, ctx->nG, ctx->zero_idx, ctx->d_packed, ctx->row_stride,
+                           ctx->N, ctx->stream));
+    QR_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return QR_OK;
+}
+
+qr_status qr_get_responses(const qr_ctx* ctx, int i, double* S_out)
+{
+    if (!ready(ctx) || !S_out || i < 0 || i >= ctx->N) return QR_EINVAL;
+    qr_ctx* c = const_cast<qr_ctx*>(ctx);
+    const size_t M = (size_t)ctx->P.M;
+    if (ctx->prec == QR_FP64) {
+        QR_CU(c, cudaMemcpyAsync(S_out, static_cast<double*>(ctx->d_S) + (size_t)i * M, sizeof(double) * M,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        QR_CU(c, cudaStreamSynchronize(ctx->stream));
+    } else {
+        std::vector<float> tmp(M);
+        QR_CU(c, cudaMemcpyAsync(tmp.data(), static_cast<float*>(ctx->d_S) + (size_t)i * M, sizeof(float) * M,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        QR_CU(c, cudaStreamSynchronize(ctx->stream));
+        for (size_t t = 0; t < M; ++t) S_out[t] = tmp[t];
+    }
+    return QR_OK;
+}
+
+qr_status qr_set_profiling(qr_ctx* ctx, int on)
+{
+    if (!ready(ctx)) return QR_EINVAL;
+    ctx->profiling = on != 0;
+    return QR_OK;
+}
+
+qr_status qr_get_stats(const qr_ctx* ctx, qr_stats_t* out)
+{
+    if (!ready(ctx) || !out) return QR_EINVAL;
+    *out = ctx->stats;
+    return QR_OK;
+}
+
+qr_status qr_philox_words(const uint32_t* ctr_key, long long n, uint32_t* out)
+{
+    if (n < 0 || (n > 0 && (!ctr_key || !out))) return QR_EINVAL;
+    if (n == 0) return QR_OK;
+    uint32_t *d_in = nullptr, *d_out = nullptr;
+    if (cudaMalloc(&d_in, sizeof(uint32_t) * 6 * (size_t)n) != cudaSuccess) return QR_ENOMEM;
+    if (cudaMalloc(&d_out, sizeof(uint32_t) * 4 * (size_t)n) != cudaSuccess) {
+        cudaFree(d_in);
+        return QR_ENOMEM;
+    }
+    qr_status s = QR_OK;
+    if (cudaMemcpy(d_in, ctr_key, sizeof(uint32_t) * 6 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        launch_philox(d_in, n, d_out, 0) != cudaSuccess ||
+        cudaMemcpy(out, d_out, sizeof(uint32_t) * 4 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        s = QR_ECUDA;
+    cudaFree(d_in);
+    cudaFree(d_out);
+    return s;
+}
+
+qr_status qr_sample(int d, const qr_nu* nu, unsigned long long seed, int instance, int i, long long m0, long long n,
+                    int j, int precision, double* u_out, double* x_out, double* z_out)
+{
+    if (d < 1 || d > kDMax || !nu || n < 0 || m0 < 0 || i < 0 || i >= 65536 || instance < 0 || instance >= 4096 ||
+        (precision != QR_FP32 && precision != QR_FP64))
+        return QR_EINVAL;
+    if (n == 0) return QR_OK;
+    QrParams P{};
+    P.d = d;
+    P.nu_kind = nu->kind;
+    P.mu = nu->kind == QR_NU_LOMAX ? nu->mu : (nu->kind == QR_NU_STUDENT2 ? 2.0 : 1.0);
+    P.inv_mu = 1.0 / P.mu;
+    P.mu_is3 = nu->kind == QR_NU_LOMAX && nu->mu == 3.0;
+    P.key0 = (uint32_t)(seed & 0xffffffffull);
+    P.key1 = (uint32_t)(seed >> 32);
+    P.instance = instance;
+    double* buf = nullptr;
+    const size_t each = (size_t)n * d;
+    if (cudaMalloc(&buf, sizeof(double) * 3 * each) != cudaSuccess) return QR_ENOMEM;
+    qr_status s = QR_OK;
+    if (launch_sample(precision, P, i, m0, n, j, buf, buf + each, buf + 2 * each, 0) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+        s = QR_ECUDA;
+    if (s == QR_OK && u_out && cudaMemcpy(u_out, buf, sizeof(double) * each, cudaMemcpyDeviceToHost) != cudaSuccess)
+        s = QR_ECUDA;
+    if (s == QR_OK && x_out &&
+        cudaMemcpy(x_out, buf + each, sizeof(double) * each, cudaMemcpyDeviceToHost) != cudaSuccess)
+        s = QR_ECUDA;
+    if (s == QR_OK && z_out &&
+        cudaMemcpy(z_out, buf + 2 * each, sizeof(double) * each, cudaMemcpyDeviceToHost) != cudaSuccess)
+        s = QR_ECUDA;
+    cudaFree(buf);
+    return s;
+}
+
+}  // extern "C"

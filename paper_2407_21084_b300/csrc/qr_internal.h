@@ -1,0 +1,72 @@
+// qr_internal.h -- types shared by the host side and the kernels of libqrmc.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/qr.h"
+
+namespace qr {
+
+constexpr int kDMax = 8;    // dimensions
+constexpr int kNMax = 256;  // time steps
+constexpr int kKMax = 7;    // max |k_l| (int8 table, small power tables)
+
+enum { QR_TAG_START = 0, QR_TAG_INCR = 1, QR_TAG_TEST = 2 };
+
+// device status bits
+enum : unsigned { ST_TIMEOUT = 1u };
+
+// counters[0] = clamp hits, counters[1] = non-finite responses,
+// counters[2] = residual (bits of a non-negative double, atomicMax)
+enum { CNT_CLAMP = 0, CNT_NONFINITE = 1, CNT_RESID = 2, CNT_N = 4 };
+
+// One entry of the coefficient table: k (int8 per dimension). The table is
+// [k = 0, then Gamma_+ = {k : first nonzero k_l > 0}] in canonical order;
+// first[e] is the first dimension in which entry e differs from entry e-1.
+struct alignas(8) GEntry {
+    signed char k[8];
+};
+
+struct QrParams {
+    int d, N, nGp, K1;  // K1 = max|k_l| + 1
+    long long M;
+    int nu_kind, mu_is3;
+    double mu, inv_mu;
+    double T, dt, sqdt;
+    double b[kDMax];
+    double sig[kDMax * kDMax];  // row-major d x d, stored with row stride d
+    int sig_diag;
+    int f_kind;
+    double f_lam, f_kap, f_c;
+    double f_s[kDMax];
+    int g_kind;  // QR_GT_*
+    double g_s[kDMax], g_kap, g_lam;
+    double fexp[kNMax];  // time factor of f at t_j
+    uint32_t key0, key1;
+    int instance;
+    double clamp_L;  // <= 0: off
+    int lattice_n;
+    int chunk;     // projection: paths per CTA
+    int n_chunks;  // ceil(M / chunk)
+};
+
+// kernel launchers (qr_kernels.cu); all asynchronous on `st`
+cudaError_t launch_paths(int prec, const QrParams& P, const GEntry* tab, const uint8_t* first,
+                         const void* packed, long long row_stride, void* S, int i_lo, int i_hi,
+                         unsigned long long* counters, unsigned* status, cudaStream_t st);
+cudaError_t launch_project(int prec, const QrParams& P, const GEntry* tab, const uint8_t* first,
+                           const void* S, double2* partial, int i_lo, int i_hi, cudaStream_t st);
+cudaError_t launch_reduce(int prec, const QrParams& P, const double2* partial, double2* alpha, int nG,
+                          int zero_idx, void* packed, long long row_stride, int i_lo, int i_hi,
+                          unsigned long long* counters, cudaStream_t st);
+cudaError_t launch_pack(int prec, const QrParams& P, const double2* alpha, int nG, int zero_idx,
+                        void* packed, long long row_stride, int rows, cudaStream_t st);
+cudaError_t launch_eval(int prec, const QrParams& P, const GEntry* tab, const uint8_t* first,
+                        const void* packed_row, const double* x, long long n, double* y, int use_g,
+                        cudaStream_t st);
+cudaError_t launch_philox(const uint32_t* ctr_key, long long n, uint32_t* out, cudaStream_t st);
+cudaError_t launch_sample(int prec, const QrParams& P, int i, long long m0, long long n, int j,
+                          double* u, double* x, double* z, cudaStream_t st);
+
+}  // namespace qr

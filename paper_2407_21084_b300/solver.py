@@ -1,0 +1,158 @@
+"""Python face of libqrmc: one Solver per QRMC problem.
+
+PyTorch is used only for device memory (device-pointer evaluation) and for
+the CUDA stream the library launches on; all arithmetic runs in libqrmc.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+from .workloads import Workload
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Solver:
+    """A QRMC problem on the GPU (wraps a qr_ctx)."""
+
+    def __init__(self, d, N, T, nu_kind, mu, gamma_kind, gamma_n, b, sigma, f_kind, f_par, g_kind, g_par, M,
+                 seed, precision=L.QR_FP64, clamp_L=0.0, stream=None, lattice_n=0, instance=0):
+        self._L = L.load()
+        self.d, self.N, self.T, self.M = int(d), int(N), float(T), int(M)
+        self.precision = precision
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64).reshape(-1)
+        fp = np.ascontiguousarray(np.atleast_1d(f_par), dtype=np.float64)
+        gp = np.ascontiguousarray(np.atleast_1d(g_par), dtype=np.float64)
+        self._keep = (b, sigma, fp, gp)
+        nu = L.QrNu(nu_kind, mu)
+        gam = L.QrGamma(gamma_kind, gamma_n)
+        f = L.QrFn(f_kind, _dp(fp), fp.size)
+        g = L.QrFn(g_kind, _dp(gp), gp.size)
+        if stream is None:
+            stream_ptr = None
+            try:
+                import torch
+
+                if torch.cuda.is_available():
+                    stream_ptr = torch.cuda.current_stream().cuda_stream
+            except Exception:  # noqa: BLE001 - torch is optional plumbing
+                stream_ptr = None
+        else:
+            stream_ptr = stream
+        opts = L.QrOpts(M, seed, precision, clamp_L, stream_ptr,
+                        L.QR_U_LATTICE if lattice_n else L.QR_U_PHILOX, lattice_n, instance)
+        self._ctx = C.c_void_p()
+        st = self._L.qr_init(C.byref(self._ctx), d, N, T, C.byref(nu), C.byref(gam), _dp(b), _dp(sigma),
+                             C.byref(f), C.byref(g), C.byref(opts))
+        if st != L.QR_OK:
+            msg = self._L.qr_last_error(self._ctx).decode() if self._ctx else ""
+            self.close()
+            raise L.QrError(st, msg)
+        n = C.c_int()
+        L.check(self._L.qr_gamma_size(self._ctx, C.byref(n)), self._ctx)
+        self.nG = n.value
+
+    @classmethod
+    def from_workload(cls, w: Workload, precision=L.QR_FP64, M=None, stream=None, clamp=True):
+        return cls(w.d, w.N, w.T, w.nu_kind, w.mu, w.gamma_kind, w.gamma_n, w.b, w.sigma, L.QR_F_CUBIC_MANUF,
+                   w.f_par, L.QR_GT_COS, w.g_par, w.M if M is None else M, w.seed, precision=precision,
+                   clamp_L=w.clamp_L if clamp else 0.0, stream=stream)
+
+    # -------------------------------------------------------------- calls
+    def picard_step(self, n_iter: int = 1) -> float:
+        r = C.c_double()
+        L.check(self._L.qr_picard_step(self._ctx, n_iter, C.byref(r)), self._ctx)
+        return r.value
+
+    def backward_sweep(self):
+        L.check(self._L.qr_backward_sweep(self._ctx), self._ctx)
+
+    def coefs(self) -> np.ndarray:
+        a = np.zeros((self.N, self.nG), dtype=np.complex128)
+        L.check(self._L.qr_get_coefs(self._ctx, _dp(a.view(np.float64))), self._ctx)
+        return a
+
+    def set_coefs(self, alpha: np.ndarray):
+        a = np.ascontiguousarray(alpha, dtype=np.complex128)
+        assert a.shape == (self.N, self.nG)
+        L.check(self._L.qr_set_coefs(self._ctx, _dp(a.view(np.float64))), self._ctx)
+
+    def gamma_list(self) -> np.ndarray:
+        k = np.zeros((self.nG, self.d), dtype=np.int32)
+        L.check(self._L.qr_gamma_list(self._ctx, k.ctypes.data_as(C.POINTER(C.c_int))), self._ctx)
+        return k
+
+    def responses(self, i: int) -> np.ndarray:
+        S = np.zeros(self.M)
+        L.check(self._L.qr_get_responses(self._ctx, i, _dp(S)), self._ctx)
+        return S
+
+    def eval(self, i: int, x):
+        """ybar_i at the rows of x: numpy (host path) or a CUDA torch tensor (device path)."""
+        try:
+            import torch
+        except ImportError:  # pragma: no cover
+            torch = None
+        if torch is not None and isinstance(x, torch.Tensor) and x.is_cuda:
+            xs = x.contiguous().to(torch.float64)
+            y = torch.empty(xs.shape[0], dtype=torch.float64, device=xs.device)
+            L.check(self._L.qr_eval(self._ctx, i, C.c_void_p(xs.data_ptr()), xs.shape[0],
+                                    C.c_void_p(y.data_ptr()), L.QR_DEVICE), self._ctx)
+            return y
+        xs = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+        y = np.zeros(xs.shape[0])
+        L.check(self._L.qr_eval(self._ctx, i, C.c_void_p(xs.ctypes.data), xs.shape[0], C.c_void_p(y.ctypes.data),
+                                L.QR_HOST), self._ctx)
+        return y
+
+    def set_profiling(self, on: bool = True):
+        L.check(self._L.qr_set_profiling(self._ctx, 1 if on else 0), self._ctx)
+
+    def stats(self) -> dict:
+        s = L.QrStats()
+        L.check(self._L.qr_get_stats(self._ctx, C.byref(s)), self._ctx)
+        return {f: getattr(s, f) for f, _ in L.QrStats._fields_}
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._L.qr_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def philox_words(ctr_key: np.ndarray) -> np.ndarray:
+    """Device Philox4x32-10 on rows (ctr0..3, key0, key1) -> rows of 4 words."""
+    lib = L.load()
+    a = np.ascontiguousarray(ctr_key, dtype=np.uint32).reshape(-1, 6)
+    out = np.zeros((a.shape[0], 4), dtype=np.uint32)
+    L.check(lib.qr_philox_words(a.ctypes.data_as(C.POINTER(C.c_uint32)), a.shape[0],
+                                out.ctypes.data_as(C.POINTER(C.c_uint32))))
+    return out
+
+
+def sample(d, nu_kind, mu, seed, instance, i, m0, n, j, precision=L.QR_FP64):
+    """Device sampler: (u, x, z) arrays of shape (n, d)."""
+    lib = L.load()
+    u = np.zeros((n, d))
+    x = np.zeros((n, d))
+    z = np.zeros((n, d))
+    nu = L.QrNu(nu_kind, mu)
+    L.check(lib.qr_sample(d, C.byref(nu), seed, instance, i, m0, n, j, precision, _dp(u), _dp(x), _dp(z)))
+    return u, x, z

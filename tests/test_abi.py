@@ -1,0 +1,87 @@
+"""CPU checks of the C-ABI boundary: the library builds for sm_103a, loads,
+exports every entry point include/qr.h declares, validates arguments on the
+host before touching a GPU, and the product path never reaches the oracle."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2407_21084_b300 import _lib, build
+
+    build.build()
+    return _lib.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "qr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qr_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    from paper_2407_21084_b300 import _lib
+
+    assert _declared() == sorted(_lib.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_sm103a_code_object(lib):
+    from paper_2407_21084_b300 import build
+
+    assert any("compute_103a" in a for a in build.ARCH)
+    data = open(build.LIB, "rb").read()
+    assert b"sm_103a" in data or b"sm_103" in data
+
+
+def _init(lib, d=2, N=4, T=1.0, gamma=(1, 2), M=64, prec=0, fkind=0, gkind=0, nu=(0, 3.0), lattice=0):
+    from paper_2407_21084_b300 import _lib as L
+
+    b = np.zeros(max(d, 1))
+    sig = np.eye(max(d, 1)).ravel()
+    par = np.ones(16)
+    ctx = C.c_void_p()
+    st = lib.qr_init(C.byref(ctx), d, N, T, C.byref(L.QrNu(*nu)), C.byref(L.QrGamma(*gamma)),
+                     b.ctypes.data_as(C.POINTER(C.c_double)), sig.ctypes.data_as(C.POINTER(C.c_double)),
+                     C.byref(L.QrFn(fkind, par.ctypes.data_as(C.POINTER(C.c_double)), 16)),
+                     C.byref(L.QrFn(gkind, par.ctypes.data_as(C.POINTER(C.c_double)), 16)),
+                     C.byref(L.QrOpts(M, 1, prec, 0.0, None, 1 if lattice else 0, lattice, 0)))
+    msg = lib.qr_last_error(ctx).decode() if ctx else ""
+    lib.qr_destroy(ctx)
+    return st, msg
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(d=0), "d must"), (dict(d=9), "d must"), (dict(N=0), "N must"), (dict(N=257), "N must"),
+    (dict(T=-1.0), "T must"), (dict(M=0), "M must"), (dict(prec=7), "precision"),
+    (dict(gamma=(5, 2)), "index set"), (dict(gamma=(0, 8)), "|k_l| <= 7"), (dict(nu=(0, -1.0)), "mu"),
+    (dict(fkind=9), "driver"), (dict(gkind=9), "terminal"), (dict(lattice=3, M=10), "lattice"),
+])
+def test_host_validation_rejects_before_any_device_work(lib, kw, frag):
+    st, msg = _init(lib, **kw)
+    assert st in (1, 6), (st, msg)
+    assert frag in msg
+
+
+def test_status_strings(lib):
+    assert lib.qr_status_string(0) == b"ok"
+    assert lib.qr_status_string(4) == b"device wait timed out"
+
+
+def test_product_never_imports_the_oracle():
+    pat = re.compile(r"(^\s*(import|from)\s+oracle\b)|liboracle|qr_oracle|ora_[a-z]", re.M)
+    pkg = os.path.join(ROOT, "paper_2407_21084_b300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                assert not pat.search(open(os.path.join(dirpath, f)).read()), f
