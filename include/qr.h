@@ -122,6 +122,9 @@ typedef struct {
                                  polynomials exactly) */
     int lattice_n;
     int instance;             /* Philox counter field, 0 <= instance < 4096 */
+    int path_kernel;          /* 0: the compile-time tree kernel when one is built for this
+                                 index set (|k|_1 or |k|_inf sets of the benchmark workloads),
+                                 else the table-driven kernel; 1: always the table-driven kernel */
 } qr_opts;
 
 /* Creates a context: validates the problem, enumerates Gamma, allocates the

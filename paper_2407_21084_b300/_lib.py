@@ -51,6 +51,7 @@ class QrOpts(C.Structure):
         ("uniform_source", C.c_int),
         ("lattice_n", C.c_int),
         ("instance", C.c_int),
+        ("path_kernel", C.c_int),
     ]
 
 

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "qr_fast.h"
 #include "qr_internal.h"
 
 using namespace qr;
@@ -33,6 +34,13 @@ struct qr_ctx {
     unsigned long long* d_counters = nullptr;
     unsigned* d_status = nullptr;
     unsigned long long* h_counters = nullptr;  // pinned
+    // tree-layout kernel (compiled for this index set): coefficient rows in
+    // traversal order, rebuilt from the master rows after every reduction
+    int gkind = 0, gn = 0;
+    int tree_slots = 0;
+    long long tree_stride = 0;
+    void* d_tree = nullptr;
+    TreeMap* d_tmap = nullptr;
     bool profiling = false;
     cudaEvent_t ev[8] = {};
     qr_stats_t stats{};
@@ -87,6 +95,93 @@ void enumerate_gamma(int kind, int d, int n, std::vector<int>& out)
     rec(0, 0, 1);
 }
 
+// Tree layout of the half set (mirrors the traversal of qr_fast.cu): the
+// root slot, then for each dimension the subtree of +e_l; a node's slot is
+// followed by its extension child and its children in the later dimensions,
+// whose + and - subtrees follow each other; +-1 leaf pairs are pre-combined.
+bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vector<TreeMap>& out)
+{
+    const int nG = (int)(K.size() / d);
+    auto key = [&](const std::vector<int>& k) {
+        long long h = 0;
+        for (int l = 0; l < d; ++l) h = h * 64 + (k[l] + 32);
+        return h;
+    };
+    std::vector<std::pair<long long, int>> idx;
+    idx.reserve(nG);
+    for (int e = 0; e < nG; ++e) idx.emplace_back(key(std::vector<int>(K.begin() + (size_t)e * d, K.begin() + (size_t)(e + 1) * d)), e);
+    std::sort(idx.begin(), idx.end());
+    auto find = [&](const std::vector<int>& k) {
+        auto it = std::lower_bound(idx.begin(), idx.end(), std::make_pair(key(k), -1));
+        return (it != idx.end() && it->first == key(k)) ? it->second : -1;
+    };
+    const bool l1 = kind == QR_G_L1;
+    auto ext_ok = [&](int S) { return l1 ? S >= 1 : S < n; };
+    auto ext_S = [&](int S) { return l1 ? S - 1 : S + 1; };
+    auto new_ok = [&](int S) { return l1 ? S >= 1 : true; };
+    auto new_S = [&](int S) { return l1 ? S - 1 : 1; };
+    auto leaf = [&](int L, int S) { return l1 ? S == 0 : (S == n && L == d - 1); };
+    bool ok = true;
+    int emitted = 0;
+    auto single = [&](const std::vector<int>& k) {
+        const int e = find(k);
+        if (e < 0) ok = false;
+        TreeMap m{};
+        m.i[0][0] = 2 * std::max(e, 0);
+        m.c[0][0] = 2.0;
+        m.i[1][0] = 2 * std::max(e, 0) + 1;
+        m.c[1][0] = 2.0;
+        out.push_back(m);
+        ++emitted;
+    };
+    auto pair = [&](const std::vector<int>& kp, const std::vector<int>& km) {
+        const int ep = std::max(find(kp), 0), em = std::max(find(km), 0);
+        if (find(kp) < 0 || find(km) < 0) ok = false;
+        TreeMap a{}, b{};
+        a.i[0][0] = 2 * ep; a.c[0][0] = 2.0; a.i[0][1] = 2 * em; a.c[0][1] = 2.0;           // A = a+ + a-
+        a.i[1][0] = 2 * em + 1; a.c[1][0] = 2.0; a.i[1][1] = 2 * ep + 1; a.c[1][1] = -2.0;  // B = b- - b+
+        b.i[0][0] = 2 * ep; b.c[0][0] = 2.0; b.i[0][1] = 2 * em; b.c[0][1] = -2.0;          // C = a+ - a-
+        b.i[1][0] = 2 * ep + 1; b.c[1][0] = 2.0; b.i[1][1] = 2 * em + 1; b.c[1][1] = 2.0;   // E = b+ + b-
+        out.push_back(a);
+        out.push_back(b);
+        emitted += 2;
+    };
+    std::function<void(int, int, std::vector<int>)> node = [&](int L, int S, std::vector<int> k) {
+        single(k);
+        if (ext_ok(S)) {
+            std::vector<int> k2 = k;
+            k2[L] += k[L] > 0 ? 1 : -1;
+            if (leaf(L, ext_S(S))) single(k2);
+            else node(L, ext_S(S), k2);
+        }
+        if (new_ok(S))
+            for (int l2 = L + 1; l2 < d; ++l2) {
+                std::vector<int> kp = k, km = k;
+                kp[l2] += 1;
+                km[l2] -= 1;
+                if (leaf(l2, new_S(S))) {
+                    pair(kp, km);
+                } else {
+                    node(l2, new_S(S), kp);
+                    node(l2, new_S(S), km);
+                }
+            }
+    };
+    std::vector<int> zero(d, 0);
+    TreeMap r{};
+    r.i[0][0] = 2 * find(zero);
+    r.c[0][0] = 1.0;
+    out.push_back(r);
+    const int S0 = l1 ? n - 1 : 1;
+    for (int l = 0; l < d; ++l) {
+        std::vector<int> k = zero;
+        k[l] = 1;
+        if (leaf(l, S0)) single(k);
+        else node(l, S0, k);
+    }
+    return ok && emitted == (nG - 1) / 2;
+}
+
 template <typename T>
 qr_status dalloc(qr_ctx* c, T** p, size_t bytes)
 {
@@ -101,7 +196,8 @@ void release(qr_ctx* c)
 {
     if (!c) return;
     if (c->stream || c->own_stream) {
-        void* ptrs[] = {c->d_tab, c->d_first, c->d_alpha, c->d_packed, c->d_S, c->d_partial, c->d_counters, c->d_status};
+        void* ptrs[] = {c->d_tab,     c->d_first,   c->d_alpha,    c->d_packed, c->d_S,
+                        c->d_partial, c->d_counters, c->d_status, c->d_tree,  c->d_tmap};
         for (void* p : ptrs)
             if (p) cudaFreeAsync(p, c->stream);
         cudaStreamSynchronize(c->stream);
@@ -150,14 +246,24 @@ void harvest(qr_ctx* c, int slot)
     }
 }
 
+cudaError_t pack_tree_rows(qr_ctx* c, int r_lo, int r_hi)
+{
+    return launch_pack_tree(c->prec, c->d_alpha + (size_t)r_lo * c->nG, c->nG, c->d_tmap, c->tree_slots,
+                            static_cast<char*>(c->d_tree) + c->elem * (size_t)r_lo * c->tree_stride, c->tree_stride,
+                            r_hi - r_lo, c->stream);
+}
+
 // one projection of rows [i_lo, i_hi) from the current packed coefficients
 qr_status run_rows(qr_ctx* c, int i_lo, int i_hi)
 {
     QR_CU(c, cudaMemsetAsync(c->d_counters + CNT_RESID, 0, sizeof(unsigned long long), c->stream));
     {
         Timer t(c, 0);
-        cudaError_t e = launch_paths(c->prec, c->P, c->d_tab, c->d_first, c->d_packed, c->row_stride, c->d_S, i_lo,
-                                     i_hi, c->d_counters, c->d_status, c->stream);
+        cudaError_t e = c->tree_slots
+                            ? launch_paths_tree(c->prec, c->gkind, c->gn, c->P, c->d_tree, c->tree_stride, c->d_S,
+                                                i_lo, i_hi, c->d_counters, c->d_status, c->stream)
+                            : launch_paths(c->prec, c->P, c->d_tab, c->d_first, c->d_packed, c->row_stride, c->d_S,
+                                           i_lo, i_hi, c->d_counters, c->d_status, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "path-and-series kernel");
     }
     harvest(c, 0);
@@ -171,6 +277,8 @@ qr_status run_rows(qr_ctx* c, int i_lo, int i_hi)
         Timer t(c, 2);
         cudaError_t e = launch_reduce(c->prec, c->P, c->d_partial, c->d_alpha, c->nG, c->zero_idx, c->d_packed,
                                       c->row_stride, i_lo, i_hi, c->d_counters, c->stream);
+        if (e == cudaSuccess && c->tree_slots)
+            e = pack_tree_rows(c, i_lo, i_hi);
         if (e != cudaSuccess) return cuda_fail(c, e, "reduction kernel");
     }
     harvest(c, 2);
@@ -252,7 +360,7 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     std::vector<uint8_t> first(c->nGp, 0);
     for (int e = 0; e < c->nGp; ++e) {
         std::memset(tab[e].k, 0, sizeof(tab[e].k));
-        for (int l = 0; l < d; ++l) tab[e].k[l] = (signed char)c->k[(size_t)(c->zero_idx + e) * d + l];
+        for (int l = 0; l < d && l < kDMax; ++l) tab[e].k[l] = (signed char)c->k[(size_t)(c->zero_idx + e) * d + l];
         if (e > 0) {
             int f0 = 0;
             while (f0 < d && tab[e].k[f0] == tab[e - 1].k[f0]) ++f0;
@@ -383,6 +491,24 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     if ((s = cu(launch_pack(c->prec, P, c->d_alpha, c->nG, c->zero_idx, c->d_packed, c->row_stride, N + 1, c->stream),
                 "pack")) != QR_OK)
         return bail(s, c->err);
+    c->gkind = gamma->kind;
+    c->gn = gamma->n;
+    if (o.path_kernel == 0 && gamma->kind != QR_G_HYP) c->tree_slots = tree_slots(gamma->kind, d, gamma->n);
+    if (c->tree_slots) {
+        std::vector<TreeMap> map;
+        if (!build_tree_map(gamma->kind, d, gamma->n, c->k, map) || (int)map.size() != c->tree_slots)
+            return bail(QR_ENOTIMPL, "tree layout does not match the compiled kernel");
+        c->tree_stride = c->prec == QR_FP32 ? ((c->tree_slots + 1) & ~1) : c->tree_slots;
+        if ((s = dalloc(c, &c->d_tmap, sizeof(TreeMap) * map.size())) != QR_OK) return bail(s, c->err);
+        if ((s = dalloc(c, &c->d_tree, c->elem * (size_t)(N + 1) * c->tree_stride)) != QR_OK) return bail(s, c->err);
+        if ((s = cu(cudaMemcpyAsync(c->d_tmap, map.data(), sizeof(TreeMap) * map.size(), cudaMemcpyHostToDevice,
+                                    c->stream),
+                    "copy tree map")) != QR_OK ||
+            (s = cu(pack_tree_rows(c, 0, N + 1), "pack tree")) != QR_OK)
+            return bail(s, c->err);
+    } else if (o.path_kernel != 0 && o.path_kernel != 1) {
+        return bail(QR_EINVAL, "unknown path kernel");
+    }
     if ((s = cu(cudaStreamSynchronize(c->stream), "init sync")) != QR_OK) return bail(s, c->err);
     *out = c;
     return QR_OK;
@@ -497,6 +623,7 @@ qr_status qr_set_coefs(qr_ctx* ctx, const double* alpha_in)
                                cudaMemcpyHostToDevice, ctx->stream));
     QR_CU(ctx, launch_pack(ctx->prec, ctx->P, ctx->d_alpha, ctx->nG, ctx->zero_idx, ctx->d_packed, ctx->row_stride,
                            ctx->N, ctx->stream));
+    if (ctx->tree_slots) QR_CU(ctx, pack_tree_rows(ctx, 0, ctx->N));
     QR_CU(ctx, cudaStreamSynchronize(ctx->stream));
     return QR_OK;
 }

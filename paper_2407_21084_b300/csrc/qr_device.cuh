@@ -338,6 +338,13 @@ __device__ __forceinline__ R term_g(const QrParams& P, const R (&x)[D])
     return (R)1 + (R)P.g_kap + rsin<R>((R)P.g_lam * sx);
 }
 
+__device__ __forceinline__ unsigned long long warp_sum_ull(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // ------------------------------------------------------ mbarrier / bulk copy
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {

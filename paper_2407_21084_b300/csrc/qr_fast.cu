@@ -1,0 +1,399 @@
+// qr_fast.cu -- path-and-series kernel specialised at compile time for the
+// |k|_1 <= n and |k|_inf <= n index sets.
+//
+// The series ybar(x) = Re sum_{k in Gamma} alpha_k phi_k(x) is evaluated over
+// the half set Gamma_+ = {0} u {k : first nonzero k_l > 0} (alpha_{-k} =
+// conj(alpha_k)), walking the "chain tree" of Gamma_+: the parent of k is k
+// with its last nonzero coordinate moved one step towards 0, so every node's
+// basis value is its parent's times a single base phase z_l or conj(z_l),
+// z_l = e^{2 pi i F_nu(x_l)}. Only the d base phases live in registers; no
+// power table is needed. Each node accumulates
+//     T_c = coef_c + sum_{leaf children ch} coef_ch w_ch
+// and contributes Re(b_c T_c); children that are leaves in a new dimension
+// come in +-1 pairs whose two coefficients are pre-combined on the host, so a
+// pair costs 4 FMA. The + and - subtrees of a new dimension share code
+// through a two-trip runtime loop (w = z or conj z), which keeps the unrolled
+// code to a few hundred tree nodes for d = 6, n = 5.
+//
+// Coefficients are stored per time row in the traversal order ("tree
+// layout", one float2/double2 slot per half-set coefficient) by k_pack_tree
+// and staged in shared memory by bulk copies, double buffered.
+#include "qr_device.cuh"
+#include "qr_fast.h"
+
+namespace qr {
+
+template <int D, int NN, int KIND>
+struct TreeShape {
+    static constexpr bool ext_ok(int S) { return KIND == QR_G_L1 ? S >= 1 : S < NN; }
+    static constexpr int ext_S(int S) { return KIND == QR_G_L1 ? S - 1 : S + 1; }
+    static constexpr bool new_ok(int S) { return KIND == QR_G_L1 ? S >= 1 : true; }
+    static constexpr int new_S(int S) { return KIND == QR_G_L1 ? S - 1 : 1; }
+    static constexpr bool leaf(int L, int S) { return KIND == QR_G_L1 ? S == 0 : (S == NN && L == D - 1); }
+    static constexpr int root_S() { return KIND == QR_G_L1 ? NN - 1 : 1; }
+    // slots of the subtree of an internal node (L, S), its own slot included
+    static constexpr int size(int L, int S)
+    {
+        int n = 1;
+        if (ext_ok(S)) n += leaf(L, ext_S(S)) ? 1 : size(L, ext_S(S));
+        if (new_ok(S))
+            for (int l2 = L + 1; l2 < D; ++l2) n += leaf(l2, new_S(S)) ? 2 : 2 * size(l2, new_S(S));
+        return n;
+    }
+    static constexpr int total()
+    {
+        int n = 1;
+        for (int l = 0; l < D; ++l) n += leaf(l, root_S()) ? 1 : size(l, root_S());
+        return n;
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ void cfma(V2<R>& t, V2<R> c, V2<R> w)
+{
+    t.x = fma(c.x, w.x, t.x);
+    t.x = fma(-c.y, w.y, t.x);
+    t.y = fma(c.x, w.y, t.y);
+    t.y = fma(c.y, w.x, t.y);
+}
+
+template <typename R, int D, int NN, int KIND, int P, int L, int S>
+struct Node;
+
+// children in the new dimensions L2 .. D-1 of a node in state S
+template <typename R, int D, int NN, int KIND, int P, int L2, int S>
+struct NewDims {
+    using Sh = TreeShape<D, NN, KIND>;
+    static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, int& off, const V2<R> (&b)[P],
+                                               V2<R> (&T)[P], const V2<R> (&z)[P][D], R (&acc)[P])
+    {
+        if constexpr (L2 < D) {
+            constexpr int S2 = Sh::new_S(S);
+            if constexpr (Sh::leaf(L2, S2)) {
+                // T += c+ z + c- conj(z), pre-combined as (A, B), (C, E):
+                // T.x += A z.x + B z.y,  T.y += C z.y + E z.x
+                const V2<R> ab = c[off], ce = c[off + 1];
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    T[p].x = fma(ab.x, z[p][L2].x, T[p].x);
+                    T[p].x = fma(ab.y, z[p][L2].y, T[p].x);
+                    T[p].y = fma(ce.x, z[p][L2].y, T[p].y);
+                    T[p].y = fma(ce.y, z[p][L2].x, T[p].y);
+                }
+                off += 2;
+            } else {
+                constexpr int sz = Sh::size(L2, S2);
+                const V2<R>* cs = c + off;
+#pragma unroll 1
+                for (int s = 0; s < 2; ++s) {
+                    V2<R> w[P], b2[P];
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        w[p] = z[p][L2];
+                        if (s) w[p].y = -w[p].y;
+                        b2[p] = cmul<R>(b[p], w[p]);
+                    }
+                    Node<R, D, NN, KIND, P, L2, S2>::run(cs + s * sz, b2, w, z, acc);
+                }
+                off += 2 * sz;
+            }
+            NewDims<R, D, NN, KIND, P, L2 + 1, S>::run(c, off, b, T, z, acc);
+        }
+    }
+};
+
+// an internal node (L, S): its slot, then the extension child, then the new dimensions
+template <typename R, int D, int NN, int KIND, int P, int L, int S>
+struct Node {
+    using Sh = TreeShape<D, NN, KIND>;
+    static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, const V2<R> (&b)[P],
+                                               const V2<R> (&wl)[P], const V2<R> (&z)[P][D], R (&acc)[P])
+    {
+        V2<R> T[P];
+        const V2<R> c0 = c[0];
+#pragma unroll
+        for (int p = 0; p < P; ++p) T[p] = c0;
+        int off = 1;
+        if constexpr (Sh::ext_ok(S)) {
+            constexpr int S2 = Sh::ext_S(S);
+            if constexpr (Sh::leaf(L, S2)) {
+                const V2<R> ce = c[off];
+#pragma unroll
+                for (int p = 0; p < P; ++p) cfma<R>(T[p], ce, wl[p]);
+                off += 1;
+            } else {
+                V2<R> b2[P];
+#pragma unroll
+                for (int p = 0; p < P; ++p) b2[p] = cmul<R>(b[p], wl[p]);
+                Node<R, D, NN, KIND, P, L, S2>::run(c + off, b2, wl, z, acc);
+                off += Sh::size(L, S2);
+            }
+        }
+        if constexpr (Sh::new_ok(S)) NewDims<R, D, NN, KIND, P, L + 1, S>::run(c, off, b, T, z, acc);
+#pragma unroll
+        for (int p = 0; p < P; ++p) acc[p] += b[p].x * T[p].x - b[p].y * T[p].y;
+    }
+};
+
+// root children (first nonzero coordinate, sign +)
+template <typename R, int D, int NN, int KIND, int P, int L>
+struct RootKids {
+    using Sh = TreeShape<D, NN, KIND>;
+    static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, int& off, V2<R> (&T)[P],
+                                               const V2<R> (&z)[P][D], R (&acc)[P])
+    {
+        if constexpr (L < D) {
+            constexpr int S0 = Sh::root_S();
+            if constexpr (Sh::leaf(L, S0)) {
+                const V2<R> ce = c[off];
+#pragma unroll
+                for (int p = 0; p < P; ++p) cfma<R>(T[p], ce, z[p][L]);
+                off += 1;
+            } else {
+                V2<R> b[P], w[P];
+#pragma unroll
+                for (int p = 0; p < P; ++p) b[p] = w[p] = z[p][L];
+                Node<R, D, NN, KIND, P, L, S0>::run(c + off, b, w, z, acc);
+                off += Sh::size(L, S0);
+            }
+            RootKids<R, D, NN, KIND, P, L + 1>::run(c, off, T, z, acc);
+        }
+    }
+};
+
+template <typename R, int D, int NN, int KIND, int P>
+__device__ __forceinline__ void tree_series(const V2<R>* __restrict__ c, const V2<R> (&z)[P][D], R (&y)[P])
+{
+    V2<R> T[P];
+    R acc[P];
+    const V2<R> c0 = c[0];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        T[p] = c0;
+        acc[p] = 0;
+    }
+    int off = 1;
+    RootKids<R, D, NN, KIND, P, 0>::run(c, off, T, z, acc);
+#pragma unroll
+    for (int p = 0; p < P; ++p) y[p] = acc[p] + T[p].x;  // b_root = 1
+}
+
+// ------------------------------------------------------ path-and-series kernel
+template <typename R, int D, int NN, int KIND, int P, int BS>
+__global__ void __launch_bounds__(BS) k_paths_tree(const __grid_constant__ QrParams P_, const V2<R>* __restrict__ tree,
+                                                   long long row_stride, R* __restrict__ S, int i_lo,
+                                                   int tiles_per_i, unsigned long long* __restrict__ counters,
+                                                   unsigned* __restrict__ status)
+{
+    const QrParams& Pm = P_;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = Pm.N;
+    const uint32_t rowbytes = (uint32_t)(row_stride * sizeof(V2<R>));
+    V2<R>* abuf[2] = {reinterpret_cast<V2<R>*>(smem), reinterpret_cast<V2<R>*>(smem + rowbytes)};
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * (size_t)rowbytes);
+
+    const int tid = threadIdx.x;
+    const int i = i_lo + (int)(blockIdx.x / tiles_per_i);
+    const long long m0 = (long long)(blockIdx.x % tiles_per_i) * (BS * P) + tid;
+    const bool trig = Pm.g_kind == QR_GT_TRIGPOLY;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    bool inflight[2] = {false, false};
+    uint32_t phase[2] = {0u, 0u};
+    if (i + 1 < N || (i + 1 == N && trig)) {
+        if (tid == 0) bulk_load(abuf[0], tree + (size_t)(i + 1) * row_stride, rowbytes, &bars[0]);
+        inflight[0] = true;
+    }
+
+    R x[P][D], sum[P], comp[P], gN[P];
+    unsigned long long hits = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        V2<R> unused[D];
+        start_point<R, D>(Pm, i, m0 + p * BS, x[p], unused, false);
+        sum[p] = comp[p] = gN[p] = 0;
+    }
+    const R dt = (R)Pm.dt;
+
+    for (int j = i; j < N; ++j) {
+        const int buf = (j - i) & 1, row = j + 1;
+        const bool use_series = row < N || trig;
+        const int nrow = row + 1;
+        if (nrow < N || (nrow == N && trig)) {
+            if (tid == 0) {
+                fence_proxy_async_smem();
+                bulk_load(abuf[buf ^ 1], tree + (size_t)nrow * row_stride, rowbytes, &bars[buf ^ 1]);
+            }
+            inflight[buf ^ 1] = true;
+        }
+        R x1[P][D], y[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            R z[D];
+            normals<R, D>(Pm, i, (uint32_t)(m0 + p * BS), j, z);
+            euler<R, D>(Pm, x[p], z, x1[p]);
+        }
+        if (use_series) {
+            const bool ok = mbar_wait(&bars[buf], phase[buf]);
+            phase[buf] ^= 1u;
+            inflight[buf] = false;
+            if (!__syncthreads_and(ok)) {
+                if (tid == 0) {
+                    atomicOr(status, ST_TIMEOUT);
+                    if (inflight[buf ^ 1]) (void)mbar_wait(&bars[buf ^ 1], phase[buf ^ 1]);
+                }
+                __syncthreads();
+                return;
+            }
+            V2<R> zz[P][D];
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+#pragma unroll
+                for (int l = 0; l < D; ++l) zz[p][l] = nu_phase<R>(Pm, x1[p][l]);
+            tree_series<R, D, NN, KIND, P>(abuf[buf], zz, y);
+            if (row < N && Pm.clamp_L > 0.0) {
+                const R Lc = (R)Pm.clamp_L;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    if (y[p] > Lc) {
+                        y[p] = Lc;
+                        if (m0 + p * BS < Pm.M) ++hits;
+                    } else if (y[p] < -Lc) {
+                        y[p] = -Lc;
+                        if (m0 + p * BS < Pm.M) ++hits;
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p) y[p] = term_g<R, D>(Pm, x1[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (row == N) gN[p] = y[p];
+            const R term = drv_f<R, D>(Pm, j, x[p], y[p]) * dt;
+            const R yk = term - comp[p];
+            const R tk = sum[p] + yk;
+            comp[p] = (tk - sum[p]) - yk;
+            sum[p] = tk;
+#pragma unroll
+            for (int l = 0; l < D; ++l) x[p][l] = x1[p][l];
+        }
+        __syncthreads();
+    }
+    unsigned long long bad = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const long long m = m0 + p * BS;
+        if (m < Pm.M) {
+            const R Sv = gN[p] + sum[p];
+            S[(size_t)(i - i_lo) * (size_t)Pm.M + (size_t)m] = Sv;
+            if (!isfinite(Sv)) ++bad;
+        }
+    }
+    hits = warp_sum_ull(hits);
+    bad = warp_sum_ull(bad);
+    if ((tid & 31) == 0) {
+        if (hits) atomicAdd(&counters[CNT_CLAMP], hits);
+        if (bad) atomicAdd(&counters[CNT_NONFINITE], bad);
+    }
+}
+
+template <typename R>
+__global__ void k_pack_tree(const double* __restrict__ alpha, int nG, const TreeMap* __restrict__ map, int slots,
+                            V2<R>* __restrict__ out, long long row_stride, int rows)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)rows * slots) return;
+    const int r = (int)(idx / slots), s = (int)(idx % slots);
+    const double* a = alpha + (size_t)r * 2 * nG;
+    const TreeMap mp = map[s];
+    double v[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        double t = 0.0;
+        if (mp.c[h][0] != 0) t += mp.c[h][0] * a[mp.i[h][0]];
+        if (mp.c[h][1] != 0) t += mp.c[h][1] * a[mp.i[h][1]];
+        v[h] = t;
+    }
+    out[(size_t)r * row_stride + s] = mk2<R>((R)v[0], (R)v[1]);
+}
+
+// ------------------------------------------------------------ dispatch
+template <int D, int NN, int KIND>
+int tree_slots_t()
+{
+    return TreeShape<D, NN, KIND>::total();
+}
+
+template <typename R, int D, int NN, int KIND>
+static cudaError_t paths_tree_t(const QrParams& P, const void* tree, long long row_stride, void* S, int i_lo,
+                                int i_hi, unsigned long long* counters, unsigned* status, cudaStream_t st)
+{
+    constexpr int PP = sizeof(R) == 4 ? 2 : 1;
+    constexpr int BS = 128;
+    const size_t sm = 2 * (size_t)row_stride * sizeof(V2<R>) + 16;
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
+    auto kern = k_paths_tree<R, D, NN, KIND, PP, BS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int tiles = (int)((P.M + BS * PP - 1) / (BS * PP));
+    const long long blocks = (long long)tiles * (i_hi - i_lo);
+    if (blocks <= 0) return cudaSuccess;
+    kern<<<(unsigned)blocks, BS, sm, st>>>(P, static_cast<const V2<R>*>(tree), row_stride, static_cast<R*>(S), i_lo,
+                                           tiles, counters, status);
+    return cudaGetLastError();
+}
+
+// (kind, d, n) sets with a compiled tree kernel
+#define QR_TREE_SETS(X)   \
+    X(QR_G_LINF, 1, 3)    \
+    X(QR_G_LINF, 2, 2)    \
+    X(QR_G_LINF, 2, 4)    \
+    X(QR_G_L1, 3, 2)      \
+    X(QR_G_L1, 4, 4)      \
+    X(QR_G_L1, 6, 5)
+
+int tree_slots(int kind, int d, int n)
+{
+#define QR_X(K, DD, NNN) \
+    if (kind == K && d == DD && n == NNN) return tree_slots_t<DD, NNN, K>();
+    QR_TREE_SETS(QR_X)
+#undef QR_X
+    return 0;
+}
+
+cudaError_t launch_paths_tree(int prec, int kind, int n, const QrParams& P, const void* tree, long long row_stride,
+                              void* S, int i_lo, int i_hi, unsigned long long* counters, unsigned* status,
+                              cudaStream_t st)
+{
+#define QR_X(K, DD, NNN)                                                                                      \
+    if (kind == K && P.d == DD && n == NNN)                                                                   \
+        return prec == QR_FP32                                                                                \
+                   ? paths_tree_t<float, DD, NNN, K>(P, tree, row_stride, S, i_lo, i_hi, counters, status, st) \
+                   : paths_tree_t<double, DD, NNN, K>(P, tree, row_stride, S, i_lo, i_hi, counters, status, st);
+    QR_TREE_SETS(QR_X)
+#undef QR_X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_pack_tree(int prec, const double2* alpha, int nG, const TreeMap* map, int slots, void* out,
+                             long long row_stride, int rows, cudaStream_t st)
+{
+    const long long total = (long long)rows * slots;
+    if (total <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    const double* a = reinterpret_cast<const double*>(alpha);
+    if (prec == QR_FP32)
+        k_pack_tree<float><<<blocks, 256, 0, st>>>(a, nG, map, slots, static_cast<float2*>(out), row_stride, rows);
+    else
+        k_pack_tree<double><<<blocks, 256, 0, st>>>(a, nG, map, slots, static_cast<double2*>(out), row_stride, rows);
+    return cudaGetLastError();
+}
+
+}  // namespace qr

@@ -1,0 +1,24 @@
+// qr_fast.h -- tree-layout path-and-series kernels (qr_fast.cu).
+#pragma once
+
+#include "qr_internal.h"
+
+namespace qr {
+
+// One slot of the tree layout: slot.x = c[0][0] a[i[0][0]] + c[0][1] a[i[0][1]],
+// slot.y likewise with row 1, where a is a master coefficient row seen as
+// 2|Gamma| doubles (re, im interleaved).
+struct TreeMap {
+    int i[2][2];
+    double c[2][2];
+};
+
+// number of slots of the compiled tree for (kind, d, n); 0 if not compiled
+int tree_slots(int kind, int d, int n);
+cudaError_t launch_paths_tree(int prec, int kind, int n, const QrParams& P, const void* tree, long long row_stride,
+                              void* S, int i_lo, int i_hi, unsigned long long* counters, unsigned* status,
+                              cudaStream_t st);
+cudaError_t launch_pack_tree(int prec, const double2* alpha, int nG, const TreeMap* map, int slots, void* out,
+                             long long row_stride, int rows, cudaStream_t st);
+
+}  // namespace qr

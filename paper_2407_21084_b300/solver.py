@@ -21,7 +21,7 @@ class Solver:
     """A QRMC problem on the GPU (wraps a qr_ctx)."""
 
     def __init__(self, d, N, T, nu_kind, mu, gamma_kind, gamma_n, b, sigma, f_kind, f_par, g_kind, g_par, M,
-                 seed, precision=L.QR_FP64, clamp_L=0.0, stream=None, lattice_n=0, instance=0):
+                 seed, precision=L.QR_FP64, clamp_L=0.0, stream=None, lattice_n=0, instance=0, path_kernel=0):
         self._L = L.load()
         self.d, self.N, self.T, self.M = int(d), int(N), float(T), int(M)
         self.precision = precision
@@ -46,7 +46,7 @@ class Solver:
         else:
             stream_ptr = stream
         opts = L.QrOpts(M, seed, precision, clamp_L, stream_ptr,
-                        L.QR_U_LATTICE if lattice_n else L.QR_U_PHILOX, lattice_n, instance)
+                        L.QR_U_LATTICE if lattice_n else L.QR_U_PHILOX, lattice_n, instance, path_kernel)
         self._ctx = C.c_void_p()
         st = self._L.qr_init(C.byref(self._ctx), d, N, T, C.byref(nu), C.byref(gam), _dp(b), _dp(sigma),
                              C.byref(f), C.byref(g), C.byref(opts))
@@ -59,10 +59,11 @@ class Solver:
         self.nG = n.value
 
     @classmethod
-    def from_workload(cls, w: Workload, precision=L.QR_FP64, M=None, stream=None, clamp=True):
+    def from_workload(cls, w: Workload, precision=L.QR_FP64, M=None, stream=None, clamp=True, path_kernel=0,
+                      instance=0):
         return cls(w.d, w.N, w.T, w.nu_kind, w.mu, w.gamma_kind, w.gamma_n, w.b, w.sigma, L.QR_F_CUBIC_MANUF,
                    w.f_par, L.QR_GT_COS, w.g_par, w.M if M is None else M, w.seed, precision=precision,
-                   clamp_L=w.clamp_L if clamp else 0.0, stream=stream)
+                   clamp_L=w.clamp_L if clamp else 0.0, stream=stream, path_kernel=path_kernel, instance=instance)
 
     # -------------------------------------------------------------- calls
     def picard_step(self, n_iter: int = 1) -> float:

@@ -69,16 +69,20 @@ def test_sampler(qr, ora, prec):
 
 
 # ------------------------------------------------------------- iteration
-def _solver(qr, w, prec, M=None, clamp=True):
-    return qr.Solver.from_workload(w, precision=prec, M=M, clamp=clamp)
+def _solver(qr, w, prec, M=None, clamp=True, kern=0):
+    return qr.Solver.from_workload(w, precision=prec, M=M, clamp=clamp, path_kernel=kern)
 
 
+TREE, TABLE = 0, 1  # path kernels: compile-time tree (default) / table-driven
+
+
+@pytest.mark.parametrize("kern", [TREE, TABLE])
 @pytest.mark.parametrize("prec", [FP64, FP32])
-def test_c1_picard_matches_oracle(qr, ora, prec):
+def test_c1_picard_matches_oracle(qr, ora, prec, kern):
     w = W.c1()
     p = ora_problem(ora, w)
     a_ref, hits_ref = ora.picard(p, w.n_iter)
-    with _solver(qr, w, prec) as s:
+    with _solver(qr, w, prec, kern=kern) as s:
         assert np.array_equal(s.gamma_list(), p.k)
         for _ in range(w.n_iter):
             s.picard_step(1)
@@ -88,13 +92,14 @@ def test_c1_picard_matches_oracle(qr, ora, prec):
             assert s.stats()["clamp_hits"] == hits_ref
 
 
+@pytest.mark.parametrize("kern", [TREE, TABLE])
 @pytest.mark.parametrize("prec", [FP64, FP32])
-def test_responses_match_oracle(qr, ora, prec):
+def test_responses_match_oracle(qr, ora, prec, kern):
     w = W.c1().with_(N=5)
     M = 3000  # ragged: not a multiple of the block or chunk size
     p = ora_problem(ora, w, M=M)
     a1, _ = ora.picard(p, 1)
-    with _solver(qr, w, prec, M=M) as s:
+    with _solver(qr, w, prec, M=M, kern=kern) as s:
         s.set_coefs(a1)
         s.picard_step(1)
         for i in (0, 2, 4):
@@ -104,15 +109,16 @@ def test_responses_match_oracle(qr, ora, prec):
             assert np.abs(S - So).max() < tol * max(1.0, np.abs(So).max())
 
 
+@pytest.mark.parametrize("kern", [TREE, TABLE])
 @pytest.mark.parametrize("prec", [FP64, FP32])
 @pytest.mark.parametrize("M", [4096, 5000, 1, 33])
-def test_c2_prefix_matches_oracle(qr, ora, prec, M):
+def test_c2_prefix_matches_oracle(qr, ora, prec, M, kern):
     """C2 (d=4, N=16, |k|_1<=4) on the first M paths, 5 iterations."""
     w = W.c2()
     n_iter = w.n_iter if M >= 4096 else 2
     p = ora_problem(ora, w, M=M)
     a_ref, _ = ora.picard(p, n_iter)
-    with _solver(qr, w, prec, M=M) as s:
+    with _solver(qr, w, prec, M=M, kern=kern) as s:
         s.picard_step(n_iter)
         assert relerr(s.coefs(), a_ref) < TOL[prec] * (1 if M >= 4096 else 10)
 
@@ -149,7 +155,7 @@ def _planted(ora, d, kind, n, seed):
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-@pytest.mark.parametrize("d,kind,n", [(2, 0, 2), (3, 1, 2)])
+@pytest.mark.parametrize("d,kind,n", [(2, 0, 2), (3, 1, 2), (3, 0, 1), (2, 1, 3)])
 def test_planted_polynomial_and_linear_driver_on_lattice(qr, ora, prec, d, kind, n):
     K, c = _planted(ora, d, kind, n, 10 + d)
     lat, N, lam = 2 * n + 1, 4, 0.7
@@ -184,7 +190,8 @@ def test_eval_matches_oracle_series(qr, ora, prec):
         assert s.eval(0, np.zeros((0, w.d))).shape == (0,)
 
 
-def test_c3_full_launch_sampled_responses(qr, ora):
+@pytest.mark.parametrize("kern", [TREE, TABLE])
+def test_c3_full_launch_sampled_responses(qr, ora, kern):
     """C3 at its full size (d=6, N=32, M=2^22, |Gamma|=3653, FP32): the launch
     geometry the benchmark times. Responses are checked path by path against
     the oracle on a sample of (i, m), from a nonzero previous iterate."""
@@ -200,7 +207,7 @@ def test_c3_full_launch_sampled_responses(qr, ora):
     a0[:, z:] = half[:, z:] * amp[z:]
     a0[:, :z] = np.conj(a0[:, z:][:, ::-1][:, : z])
     a0[:, z] = a0[:, z].real + 0.5
-    with _solver(qr, w, FP32) as s:
+    with _solver(qr, w, FP32, kern=kern) as s:
         s.set_coefs(a0)
         s.picard_step(1)
         for i in (0, 13, w.N - 1):
@@ -213,3 +220,15 @@ def test_c3_full_launch_sampled_responses(qr, ora):
         assert np.all(np.isfinite(a))
         st = s.stats()
         assert st["nonfinite"] == 0
+
+
+def test_tree_and_table_kernels_agree_on_c3_prefix(qr):
+    """The two path kernels order the series sum differently; on the d=6,
+    |k|_1<=5 set they must agree to FP32 rounding."""
+    w = W.c3()
+    a = []
+    for kern in (TREE, TABLE):
+        with _solver(qr, w, FP32, M=8192, kern=kern) as s:
+            s.picard_step(2)
+            a.append(s.coefs())
+    assert relerr(a[0], a[1]) < 1e-5
