@@ -195,6 +195,36 @@ qr_status qr_sample(int d, const qr_nu* nu, unsigned long long seed, int instanc
                     long long m0, long long n, int j, int precision, double* u_out,
                     double* x_out, double* z_out);
 
+/* ---- projection without device allocation -----------------------------
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory when they run it: code that owns a fixed
+ * memory budget handed out up front, code running where a cudaMalloc could
+ * block or fail at an unpredictable moment (a latency-bound serving loop, a
+ * driver running under another framework's allocator). qr_picard_step keeps
+ * its cross-block partial sums in memory the context allocated; this call
+ * keeps them in a fixed array compiled into libqrmc instead (16 MiB per GPU
+ * that loads the library, held until the process exits), so it allocates
+ * nothing itself.
+ *
+ * Computes coefficient rows i in [i_lo, i_hi) from responses S given by the
+ * caller: alpha_{i,k} = (1/M) sum_m S_i^m conj(phi_k(U_i^m)), with the start
+ * uniforms U regenerated from the context's seed, exactly as the projection
+ * inside qr_picard_step does.
+ *   S:         device array, (i_hi - i_lo) rows of M responses, row-major, in
+ *              the context's precision (float for QR_FP32, double for QR_FP64).
+ *   alpha_out: device array, (i_hi - i_lo) rows of |Gamma| complex values as
+ *              interleaved (re, im) doubles, canonical order.
+ * Requires (i_hi - i_lo) * n_chunks * (|Gamma|+1)/2 <= 2^20 partial sums,
+ * n_chunks = ceil(M / chunk) <= 256; otherwise returns QR_EINVAL with the
+ * sizes in qr_last_error (project fewer rows per call).
+ * The call is asynchronous on the context's stream. The first call on a
+ * device looks up the device address of the fixed array (once per device);
+ * make that first call before any stream capture. Every call on a GPU shares
+ * the one array, and each call overwrites every slot it reads, so nothing
+ * carries over between calls; calls that can overlap on the GPU (different
+ * streams or contexts, or several host threads) race on it. */
+qr_status qr_project_static(qr_ctx* ctx, const void* S, int i_lo, int i_hi, double* alpha_out);
+
 #ifdef __cplusplus
 }
 #endif

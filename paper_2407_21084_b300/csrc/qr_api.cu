@@ -287,6 +287,26 @@ qr_status run_rows(qr_ctx* c, int i_lo, int i_hi)
 
 }  // namespace
 
+namespace qr {
+bool ctx_view(const qr_ctx* c, CtxView* v)
+{
+    if (!c || !c->d_packed || !v) return false;
+    v->prec = c->prec;
+    v->N = c->N;
+    v->nG = c->nG;
+    v->zero_idx = c->zero_idx;
+    v->P = &c->P;
+    v->tab = c->d_tab;
+    v->first = c->d_first;
+    v->stream = c->stream;
+    return true;
+}
+void ctx_set_error(qr_ctx* c, const char* msg)
+{
+    if (c) c->err = msg;
+}
+}  // namespace qr
+
 extern "C" {
 
 const char* qr_status_string(qr_status s)

@@ -69,4 +69,18 @@ cudaError_t launch_philox(const uint32_t* ctr_key, long long n, uint32_t* out, c
 cudaError_t launch_sample(int prec, const QrParams& P, int i, long long m0, long long n, int j,
                           double* u, double* x, double* z, cudaStream_t st);
 
+// read-only view of a context's device problem description (qr_api.cu)
+struct CtxView {
+    int prec, N, nG, zero_idx;
+    const QrParams* P;
+    const GEntry* tab;
+    const uint8_t* first;
+    cudaStream_t stream;
+};
+}  // namespace qr
+
+struct qr_ctx;
+namespace qr {
+bool ctx_view(const qr_ctx* c, CtxView* v);
+void ctx_set_error(qr_ctx* c, const char* msg);
 }  // namespace qr
