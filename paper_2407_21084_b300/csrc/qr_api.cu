@@ -41,6 +41,8 @@ struct qr_ctx {
     long long tree_stride = 0;
     void* d_tree = nullptr;
     TreeMap* d_tmap = nullptr;
+    int proj_nodes = 0;  // tiled projection kernel compiled for this set
+    int* d_perm = nullptr;
     bool profiling = false;
     cudaEvent_t ev[8] = {};
     qr_stats_t stats{};
@@ -182,6 +184,50 @@ bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vect
     return ok && emitted == (nG - 1) / 2;
 }
 
+// Order of the half set in the tiled projection (mirrors qr_proj_tree.cu):
+// depth-first along the chain tree with both signs of every new dimension
+// expanded; perm[s] = canonical half-set index (>= 1) of the s-th node.
+bool build_proj_perm(int kind, int d, int n, const std::vector<int>& K, int zero_idx, std::vector<int>& perm)
+{
+    const int nG = (int)(K.size() / d);
+    std::vector<std::pair<std::vector<int>, int>> idx;
+    for (int e = 0; e < nG; ++e)
+        idx.emplace_back(std::vector<int>(K.begin() + (size_t)e * d, K.begin() + (size_t)(e + 1) * d), e);
+    std::sort(idx.begin(), idx.end());
+    auto find = [&](const std::vector<int>& k) {
+        auto it = std::lower_bound(idx.begin(), idx.end(), std::make_pair(k, -1));
+        return (it != idx.end() && it->first == k) ? it->second : -1;
+    };
+    const bool l1 = kind == QR_G_L1;
+    bool ok = true;
+    std::function<void(int, int, std::vector<int>)> visit = [&](int L, int S, std::vector<int> k) {
+        const int e = find(k);
+        if (e <= zero_idx) ok = false;
+        perm.push_back(e - zero_idx);
+        if (l1 ? S >= 1 : S < n) {
+            std::vector<int> k2 = k;
+            k2[L] += k[L] > 0 ? 1 : -1;
+            visit(L, l1 ? S - 1 : S + 1, k2);
+        }
+        if (l1 ? S >= 1 : true)
+            for (int l2 = L + 1; l2 < d; ++l2) {
+                std::vector<int> kp = k, km = k;
+                kp[l2] += 1;
+                km[l2] -= 1;
+                visit(l2, l1 ? S - 1 : 1, kp);
+                visit(l2, l1 ? S - 1 : 1, km);
+            }
+    };
+    for (int l = 0; l < d; ++l) {
+        std::vector<int> k(d, 0);
+        k[l] = 1;
+        visit(l, l1 ? n - 1 : 1, k);
+    }
+    std::vector<int> seen(perm);
+    std::sort(seen.begin(), seen.end());
+    return ok && (int)perm.size() == (nG - 1) / 2 && std::unique(seen.begin(), seen.end()) == seen.end();
+}
+
 template <typename T>
 qr_status dalloc(qr_ctx* c, T** p, size_t bytes)
 {
@@ -197,7 +243,7 @@ void release(qr_ctx* c)
     if (!c) return;
     if (c->stream || c->own_stream) {
         void* ptrs[] = {c->d_tab,     c->d_first,   c->d_alpha,    c->d_packed, c->d_S,
-                        c->d_partial, c->d_counters, c->d_status, c->d_tree,  c->d_tmap};
+                        c->d_partial, c->d_counters, c->d_status, c->d_tree,  c->d_tmap, c->d_perm};
         for (void* p : ptrs)
             if (p) cudaFreeAsync(p, c->stream);
         cudaStreamSynchronize(c->stream);
@@ -269,7 +315,10 @@ qr_status run_rows(qr_ctx* c, int i_lo, int i_hi)
     harvest(c, 0);
     {
         Timer t(c, 1);
-        cudaError_t e = launch_project(c->prec, c->P, c->d_tab, c->d_first, c->d_S, c->d_partial, i_lo, i_hi, c->stream);
+        cudaError_t e = c->proj_nodes ? launch_project_tree(c->prec, c->gkind, c->gn, c->P, c->d_S, c->d_perm,
+                                                            c->d_partial, i_lo, i_hi, c->stream)
+                                      : launch_project(c->prec, c->P, c->d_tab, c->d_first, c->d_S, c->d_partial,
+                                                       i_lo, i_hi, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "projection kernel");
     }
     harvest(c, 1);
@@ -528,6 +577,17 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
             return bail(s, c->err);
     } else if (o.path_kernel != 0 && o.path_kernel != 1) {
         return bail(QR_EINVAL, "unknown path kernel");
+    }
+    if (o.path_kernel == 0 && gamma->kind != QR_G_HYP) c->proj_nodes = proj_tree_nodes(gamma->kind, d, gamma->n);
+    if (c->proj_nodes) {
+        std::vector<int> perm;
+        if (!build_proj_perm(gamma->kind, d, gamma->n, c->k, c->zero_idx, perm) || (int)perm.size() != c->proj_nodes)
+            return bail(QR_ENOTIMPL, "projection order does not match the compiled kernel");
+        if ((s = dalloc(c, &c->d_perm, sizeof(int) * perm.size())) != QR_OK) return bail(s, c->err);
+        if ((s = cu(cudaMemcpyAsync(c->d_perm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice,
+                                    c->stream),
+                    "copy projection order")) != QR_OK)
+            return bail(s, c->err);
     }
     if ((s = cu(cudaStreamSynchronize(c->stream), "init sync")) != QR_OK) return bail(s, c->err);
     *out = c;

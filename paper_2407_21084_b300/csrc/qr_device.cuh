@@ -263,6 +263,21 @@ __device__ __forceinline__ void start_point(const QrParams& P, int i, long long 
     }
 }
 
+// Phases e^{2 pi i U_l} of the exact start uniforms of path (i, m)
+template <typename R, int D>
+__device__ __forceinline__ void start_phases_dev(const QrParams& P, int i, long long m, V2<R> (&ph)[D])
+{
+    if (P.lattice_n > 0) {
+        R x[D];
+        start_point<R, D>(P, i, m, x, ph, true);
+        return;
+    }
+    uint64_t n[D];
+    start_ints<D>(P, i, (uint32_t)m, n);
+#pragma unroll
+    for (int l = 0; l < D; ++l) ph[l] = u_phase<R>(n[l]);
+}
+
 // Euler step of Sec. 2.1.1 with constant b and sigma
 template <typename R, int D>
 __device__ __forceinline__ void euler(const QrParams& P, const R (&x)[D], const R (&z)[D], R (&x1)[D])

@@ -57,6 +57,127 @@ __device__ __forceinline__ void cfma(V2<R>& t, V2<R> c, V2<R> w)
     t.y = fma(c.y, w.x, t.y);
 }
 
+// ---- per-step helpers of the tree kernel with the problem constants
+// converted once to R (no FP64 instruction per step in the FP32 form)
+template <typename R, int D>
+struct StepConsts {
+    R dt, sqdt, Lc, fc, glam, gkap, flam, fkap;
+    R b[D], sig[D * D], fs[D], gs[D];
+    bool clamp, sig_diag;
+    __device__ __forceinline__ explicit StepConsts(const QrParams& P)
+    {
+        dt = (R)P.dt;
+        sqdt = (R)P.sqdt;
+        Lc = (R)P.clamp_L;
+        clamp = P.clamp_L > 0.0;
+        fc = (R)P.f_c;
+        flam = (R)P.f_lam;
+        fkap = (R)P.f_kap;
+        glam = (R)P.g_lam;
+        gkap = (R)P.g_kap;
+        sig_diag = P.sig_diag != 0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            b[l] = (R)P.b[l];
+            fs[l] = (R)P.f_s[l];
+            gs[l] = (R)P.g_s[l];
+        }
+#pragma unroll
+        for (int t = 0; t < D * D; ++t) sig[t] = (R)P.sig[t];
+    }
+};
+
+// uniform (2n+1) 2^-53, n = (a << 20) ^ (b >> 12), from 32-bit conversions
+__device__ __forceinline__ float u01_f32(uint32_t a, uint32_t b)
+{
+    return fmaf((float)(b >> 12), 0x1p-52f, fmaf((float)a, 0x1p-32f, 0x1p-53f));
+}
+
+template <typename R, int D>
+__device__ __forceinline__ void normals_fast(const QrParams& P, int i, uint32_t m, int j, R (&z)[D])
+{
+    if constexpr (sizeof(R) == 8) {
+        normals<R, D>(P, i, m, j, z);
+    } else {
+        const uint2 key = make_uint2(P.key0, P.key1);
+#pragma unroll
+        for (int c = 0; 2 * c < D; ++c) {
+            const uint4 r = philox4x32_10(make_uint4(m, (uint32_t)c, (uint32_t)j, ctr_hi(P.instance, QR_TAG_INCR, i)), key);
+            // ln(u_a): u_a < 1/2 iff the top bit of r.x is clear; above 1/2 use log1p(-(1 - u_a)),
+            // 1 - u_a having the complemented bits
+            const float la = (r.x & 0x80000000u) ? log1pf(-u01_f32(~r.x, ~r.y)) : logf(u01_f32(r.x, r.y));
+            const float rho = sqrtf(-2.0f * la);
+            float sn, cs;
+            sincospif(2.0f * u01_f32(r.z, r.w), &sn, &cs);
+            z[2 * c] = rho * cs;
+            if (2 * c + 1 < D) z[2 * c + 1] = rho * sn;
+        }
+    }
+}
+
+template <typename R, int D>
+__device__ __forceinline__ void euler_fast(const StepConsts<R, D>& K, const R (&x)[D], const R (&z)[D], R (&x1)[D])
+{
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        R noise;
+        if (K.sig_diag) {
+            noise = K.sig[l * D + l] * z[l];
+        } else {
+            noise = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) noise += K.sig[l * D + c] * z[c];
+        }
+        x1[l] = x[l] + K.b[l] * K.dt + noise * K.sqdt;
+    }
+}
+
+template <typename R, int D>
+__device__ __forceinline__ R drv_f_fast(const QrParams& P, const StepConsts<R, D>& K, R fexp_j, const R (&x)[D], R y)
+{
+    switch (P.f_kind) {
+    case QR_F_LINEAR:
+        return K.flam * y;
+    case QR_F_CUBIC_MANUF: {
+        R sx = 0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) sx += K.fs[l] * x[l];
+        const R u = fexp_j * rcos<R>(sx);
+        return -y * y * y + (K.fc * u + u * u * u);
+    }
+    case QR_F_PAPER_MIN: {
+        R sx = 0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) sx += x[l];
+        R v = y - K.fkap - (R)1 - rsin<R>(K.flam * sx) * fexp_j;
+        v = v * v;
+        return v < (R)1 ? v : (R)1;
+    }
+    default:
+        return (R)0;
+    }
+}
+
+template <typename R, int D>
+__device__ __forceinline__ R term_g_fast(const QrParams& P, const StepConsts<R, D>& K, const R (&x)[D])
+{
+    R sx = 0;
+    if (P.g_kind == QR_GT_COS) {
+#pragma unroll
+        for (int l = 0; l < D; ++l) sx += K.gs[l] * x[l];
+        return rcos<R>(sx);
+    }
+#pragma unroll
+    for (int l = 0; l < D; ++l) sx += x[l];
+    return (R)1 + K.gkap + rsin<R>(K.glam * sx);
+}
+
+// subtrees of at most this many slots have both signs unrolled
+#ifndef QR_TREE_UNROLL
+#define QR_TREE_UNROLL 8
+#endif
+constexpr int kUnrollSlots = QR_TREE_UNROLL;
+
 template <typename R, int D, int NN, int KIND, int P, int L, int S>
 struct Node;
 
@@ -84,16 +205,33 @@ struct NewDims {
             } else {
                 constexpr int sz = Sh::size(L2, S2);
                 const V2<R>* cs = c + off;
-#pragma unroll 1
-                for (int s = 0; s < 2; ++s) {
+                if constexpr (sz <= kUnrollSlots) {
+                    // small subtrees: both signs unrolled (no loop control)
                     V2<R> w[P], b2[P];
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
                         w[p] = z[p][L2];
-                        if (s) w[p].y = -w[p].y;
                         b2[p] = cmul<R>(b[p], w[p]);
                     }
-                    Node<R, D, NN, KIND, P, L2, S2>::run(cs + s * sz, b2, w, z, acc);
+                    Node<R, D, NN, KIND, P, L2, S2>::run(cs, b2, w, z, acc);
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        w[p].y = -w[p].y;
+                        b2[p] = cmul<R>(b[p], w[p]);
+                    }
+                    Node<R, D, NN, KIND, P, L2, S2>::run(cs + sz, b2, w, z, acc);
+                } else {
+#pragma unroll 1
+                    for (int s = 0; s < 2; ++s) {
+                        V2<R> w[P], b2[P];
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            w[p] = z[p][L2];
+                            if (s) w[p].y = -w[p].y;
+                            b2[p] = cmul<R>(b[p], w[p]);
+                        }
+                        Node<R, D, NN, KIND, P, L2, S2>::run(cs + s * sz, b2, w, z, acc);
+                    }
                 }
                 off += 2 * sz;
             }
@@ -210,6 +348,7 @@ __global__ void __launch_bounds__(BS) k_paths_tree(const __grid_constant__ QrPar
         inflight[0] = true;
     }
 
+    const StepConsts<R, D> K(Pm);
     R x[P][D], sum[P], comp[P], gN[P];
     unsigned long long hits = 0;
 #pragma unroll
@@ -218,12 +357,13 @@ __global__ void __launch_bounds__(BS) k_paths_tree(const __grid_constant__ QrPar
         start_point<R, D>(Pm, i, m0 + p * BS, x[p], unused, false);
         sum[p] = comp[p] = gN[p] = 0;
     }
-    const R dt = (R)Pm.dt;
+    const R dt = K.dt;
 
     for (int j = i; j < N; ++j) {
         const int buf = (j - i) & 1, row = j + 1;
         const bool use_series = row < N || trig;
         const int nrow = row + 1;
+        const R fexp_j = (R)Pm.fexp[j];
         if (nrow < N || (nrow == N && trig)) {
             if (tid == 0) {
                 fence_proxy_async_smem();
@@ -235,8 +375,8 @@ __global__ void __launch_bounds__(BS) k_paths_tree(const __grid_constant__ QrPar
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             R z[D];
-            normals<R, D>(Pm, i, (uint32_t)(m0 + p * BS), j, z);
-            euler<R, D>(Pm, x[p], z, x1[p]);
+            normals_fast<R, D>(Pm, i, (uint32_t)(m0 + p * BS), j, z);
+            euler_fast<R, D>(K, x[p], z, x1[p]);
         }
         if (use_series) {
             const bool ok = mbar_wait(&bars[buf], phase[buf]);
@@ -256,8 +396,8 @@ __global__ void __launch_bounds__(BS) k_paths_tree(const __grid_constant__ QrPar
 #pragma unroll
                 for (int l = 0; l < D; ++l) zz[p][l] = nu_phase<R>(Pm, x1[p][l]);
             tree_series<R, D, NN, KIND, P>(abuf[buf], zz, y);
-            if (row < N && Pm.clamp_L > 0.0) {
-                const R Lc = (R)Pm.clamp_L;
+            if (row < N && K.clamp) {
+                const R Lc = K.Lc;
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     if (y[p] > Lc) {
@@ -271,12 +411,12 @@ __global__ void __launch_bounds__(BS) k_paths_tree(const __grid_constant__ QrPar
             }
         } else {
 #pragma unroll
-            for (int p = 0; p < P; ++p) y[p] = term_g<R, D>(Pm, x1[p]);
+            for (int p = 0; p < P; ++p) y[p] = term_g_fast<R, D>(Pm, K, x1[p]);
         }
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (row == N) gN[p] = y[p];
-            const R term = drv_f<R, D>(Pm, j, x[p], y[p]) * dt;
+            const R term = drv_f_fast<R, D>(Pm, K, fexp_j, x[p], y[p]) * dt;
             const R yk = term - comp[p];
             const R tk = sum[p] + yk;
             comp[p] = (tk - sum[p]) - yk;
@@ -335,7 +475,10 @@ template <typename R, int D, int NN, int KIND>
 static cudaError_t paths_tree_t(const QrParams& P, const void* tree, long long row_stride, void* S, int i_lo,
                                 int i_hi, unsigned long long* counters, unsigned* status, cudaStream_t st)
 {
-    constexpr int PP = sizeof(R) == 4 ? 2 : 1;
+#ifndef QR_TREE_P32
+#define QR_TREE_P32 2
+#endif
+    constexpr int PP = sizeof(R) == 4 ? QR_TREE_P32 : 1;  // paths per thread
     constexpr int BS = 128;
     const size_t sm = 2 * (size_t)row_stride * sizeof(V2<R>) + 16;
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;

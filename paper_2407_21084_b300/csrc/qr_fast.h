@@ -21,4 +21,10 @@ cudaError_t launch_paths_tree(int prec, int kind, int n, const QrParams& P, cons
 cudaError_t launch_pack_tree(int prec, const double2* alpha, int nG, const TreeMap* map, int slots, void* out,
                              long long row_stride, int rows, cudaStream_t st);
 
+// projection specialised for the same sets (qr_proj_tree.cu): partial sums
+// are written in canonical half-set order through perm (tree slot -> e >= 1)
+int proj_tree_nodes(int kind, int d, int n);
+cudaError_t launch_project_tree(int prec, int kind, int n, const QrParams& P, const void* S, const int* perm,
+                                double2* partial, int i_lo, int i_hi, cudaStream_t st);
+
 }  // namespace qr
