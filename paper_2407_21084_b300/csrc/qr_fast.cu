@@ -7,9 +7,10 @@
 // with its last nonzero coordinate moved one step towards 0, so every node's
 // basis value is its parent's times a single base phase z_l or conj(z_l),
 // z_l = e^{2 pi i F_nu(x_l)}. Only the d base phases live in registers; no
-// power table is needed. Each node accumulates
-//     T_c = coef_c + sum_{leaf children ch} coef_ch w_ch
-// and contributes Re(b_c T_c); children that are leaves in a new dimension
+// power table is needed. The tree is evaluated bottom-up (Horner): the value
+// of a subtree in its root's frame is
+//     V_c = coef_c + sum_{children ch} w_ch V_ch,
+// and ybar = Re V_0, one complex FMA per tree edge. Children that are leaves in a new dimension
 // come in +-1 pairs whose two coefficients are pre-combined on the host, so a
 // pair costs 4 FMA. The + and - subtrees of a new dimension share code
 // through a two-trip runtime loop (w = z or conj z), which keeps the unrolled
@@ -181,12 +182,27 @@ constexpr int kUnrollSlots = QR_TREE_UNROLL;
 template <typename R, int D, int NN, int KIND, int P, int L, int S>
 struct Node;
 
+// t += w v (complex), 4 FMA
+template <typename R>
+__device__ __forceinline__ void cmad(V2<R>& t, V2<R> w, V2<R> v)
+{
+    t.x = fma(w.x, v.x, t.x);
+    t.x = fma(-w.y, v.y, t.x);
+    t.y = fma(w.x, v.y, t.y);
+    t.y = fma(w.y, v.x, t.y);
+}
+
+// Bottom-up (Horner) evaluation: the value of the subtree of node c in its
+// own frame is V_c = coef_c + sum_children w_ch V_ch, and the series is
+// Re V_root. Every tree edge costs one complex FMA (4 FMA); a +-1 leaf pair
+// costs 4 FMA for both leaves; no prefix products are formed.
+
 // children in the new dimensions L2 .. D-1 of a node in state S
 template <typename R, int D, int NN, int KIND, int P, int L2, int S>
 struct NewDims {
     using Sh = TreeShape<D, NN, KIND>;
-    static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, int& off, const V2<R> (&b)[P],
-                                               V2<R> (&T)[P], const V2<R> (&z)[P][D], R (&acc)[P])
+    static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, int& off, V2<R> (&T)[P],
+                                               const V2<R> (&z)[P][D])
     {
         if constexpr (L2 < D) {
             constexpr int S2 = Sh::new_S(S);
@@ -207,47 +223,47 @@ struct NewDims {
                 const V2<R>* cs = c + off;
                 if constexpr (sz <= kUnrollSlots) {
                     // small subtrees: both signs unrolled (no loop control)
-                    V2<R> w[P], b2[P];
+                    V2<R> w[P], v[P];
+#pragma unroll
+                    for (int p = 0; p < P; ++p) w[p] = z[p][L2];
+                    Node<R, D, NN, KIND, P, L2, S2>::value(cs, w, z, v);
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
-                        w[p] = z[p][L2];
-                        b2[p] = cmul<R>(b[p], w[p]);
-                    }
-                    Node<R, D, NN, KIND, P, L2, S2>::run(cs, b2, w, z, acc);
-#pragma unroll
-                    for (int p = 0; p < P; ++p) {
+                        cmad<R>(T[p], w[p], v[p]);
                         w[p].y = -w[p].y;
-                        b2[p] = cmul<R>(b[p], w[p]);
                     }
-                    Node<R, D, NN, KIND, P, L2, S2>::run(cs + sz, b2, w, z, acc);
+                    Node<R, D, NN, KIND, P, L2, S2>::value(cs + sz, w, z, v);
+#pragma unroll
+                    for (int p = 0; p < P; ++p) cmad<R>(T[p], w[p], v[p]);
                 } else {
 #pragma unroll 1
                     for (int s = 0; s < 2; ++s) {
-                        V2<R> w[P], b2[P];
+                        V2<R> w[P], v[P];
 #pragma unroll
                         for (int p = 0; p < P; ++p) {
                             w[p] = z[p][L2];
                             if (s) w[p].y = -w[p].y;
-                            b2[p] = cmul<R>(b[p], w[p]);
                         }
-                        Node<R, D, NN, KIND, P, L2, S2>::run(cs + s * sz, b2, w, z, acc);
+                        Node<R, D, NN, KIND, P, L2, S2>::value(cs + s * sz, w, z, v);
+#pragma unroll
+                        for (int p = 0; p < P; ++p) cmad<R>(T[p], w[p], v[p]);
                     }
                 }
                 off += 2 * sz;
             }
-            NewDims<R, D, NN, KIND, P, L2 + 1, S>::run(c, off, b, T, z, acc);
+            NewDims<R, D, NN, KIND, P, L2 + 1, S>::run(c, off, T, z);
         }
     }
 };
 
-// an internal node (L, S): its slot, then the extension child, then the new dimensions
+// an internal node (L, S) reached through the phase wl: its slot, then the
+// extension child (same dimension, same phase), then the new dimensions
 template <typename R, int D, int NN, int KIND, int P, int L, int S>
 struct Node {
     using Sh = TreeShape<D, NN, KIND>;
-    static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, const V2<R> (&b)[P],
-                                               const V2<R> (&wl)[P], const V2<R> (&z)[P][D], R (&acc)[P])
+    static __device__ __forceinline__ void value(const V2<R>* __restrict__ c, const V2<R> (&wl)[P],
+                                                 const V2<R> (&z)[P][D], V2<R> (&T)[P])
     {
-        V2<R> T[P];
         const V2<R> c0 = c[0];
 #pragma unroll
         for (int p = 0; p < P; ++p) T[p] = c0;
@@ -260,16 +276,14 @@ struct Node {
                 for (int p = 0; p < P; ++p) cfma<R>(T[p], ce, wl[p]);
                 off += 1;
             } else {
-                V2<R> b2[P];
+                V2<R> v[P];
+                Node<R, D, NN, KIND, P, L, S2>::value(c + off, wl, z, v);
 #pragma unroll
-                for (int p = 0; p < P; ++p) b2[p] = cmul<R>(b[p], wl[p]);
-                Node<R, D, NN, KIND, P, L, S2>::run(c + off, b2, wl, z, acc);
+                for (int p = 0; p < P; ++p) cmad<R>(T[p], wl[p], v[p]);
                 off += Sh::size(L, S2);
             }
         }
-        if constexpr (Sh::new_ok(S)) NewDims<R, D, NN, KIND, P, L + 1, S>::run(c, off, b, T, z, acc);
-#pragma unroll
-        for (int p = 0; p < P; ++p) acc[p] += b[p].x * T[p].x - b[p].y * T[p].y;
+        if constexpr (Sh::new_ok(S)) NewDims<R, D, NN, KIND, P, L + 1, S>::run(c, off, T, z);
     }
 };
 
@@ -278,7 +292,7 @@ template <typename R, int D, int NN, int KIND, int P, int L>
 struct RootKids {
     using Sh = TreeShape<D, NN, KIND>;
     static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, int& off, V2<R> (&T)[P],
-                                               const V2<R> (&z)[P][D], R (&acc)[P])
+                                               const V2<R> (&z)[P][D])
     {
         if constexpr (L < D) {
             constexpr int S0 = Sh::root_S();
@@ -288,13 +302,15 @@ struct RootKids {
                 for (int p = 0; p < P; ++p) cfma<R>(T[p], ce, z[p][L]);
                 off += 1;
             } else {
-                V2<R> b[P], w[P];
+                V2<R> w[P], v[P];
 #pragma unroll
-                for (int p = 0; p < P; ++p) b[p] = w[p] = z[p][L];
-                Node<R, D, NN, KIND, P, L, S0>::run(c + off, b, w, z, acc);
+                for (int p = 0; p < P; ++p) w[p] = z[p][L];
+                Node<R, D, NN, KIND, P, L, S0>::value(c + off, w, z, v);
+#pragma unroll
+                for (int p = 0; p < P; ++p) cmad<R>(T[p], w[p], v[p]);
                 off += Sh::size(L, S0);
             }
-            RootKids<R, D, NN, KIND, P, L + 1>::run(c, off, T, z, acc);
+            RootKids<R, D, NN, KIND, P, L + 1>::run(c, off, T, z);
         }
     }
 };
@@ -303,17 +319,13 @@ template <typename R, int D, int NN, int KIND, int P>
 __device__ __forceinline__ void tree_series(const V2<R>* __restrict__ c, const V2<R> (&z)[P][D], R (&y)[P])
 {
     V2<R> T[P];
-    R acc[P];
     const V2<R> c0 = c[0];
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-        T[p] = c0;
-        acc[p] = 0;
-    }
+    for (int p = 0; p < P; ++p) T[p] = c0;
     int off = 1;
-    RootKids<R, D, NN, KIND, P, 0>::run(c, off, T, z, acc);
+    RootKids<R, D, NN, KIND, P, 0>::run(c, off, T, z);
 #pragma unroll
-    for (int p = 0; p < P; ++p) y[p] = acc[p] + T[p].x;  // b_root = 1
+    for (int p = 0; p < P; ++p) y[p] = T[p].x;
 }
 
 // ------------------------------------------------------ path-and-series kernel
