@@ -43,6 +43,10 @@ struct qr_ctx {
     TreeMap* d_tmap = nullptr;
     int proj_nodes = 0;  // tiled projection kernel compiled for this set
     int* d_perm = nullptr;
+    // one Picard iteration captured as a CUDA graph (built on first use when
+    // profiling is off and the stream can be captured)
+    cudaGraphExec_t graph = nullptr;
+    bool graph_failed = false;
     bool profiling = false;
     cudaEvent_t ev[8] = {};
     qr_stats_t stats{};
@@ -251,6 +255,7 @@ void release(qr_ctx* c)
     if (c->h_counters) cudaFreeHost(c->h_counters);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -607,9 +612,34 @@ qr_status qr_picard_step(qr_ctx* ctx, int n_iter, double* residual_out)
 {
     if (!ready(ctx)) return QR_EINVAL;
     if (n_iter < 0) return fail(ctx, QR_EINVAL, "n_iter must be >= 0");
+    QR_CU(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
+    if (!ctx->profiling && !ctx->graph && !ctx->graph_failed && n_iter > 0) {
+        // capture one iteration; streams that cannot be captured (the legacy
+        // default stream) keep the direct launches
+        cudaGraph_t g = nullptr;
+        bool ok = ctx->stream != nullptr &&
+                  cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            qr_status s = run_rows(ctx, 0, ctx->N);
+            cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+            ok = s == QR_OK && e == cudaSuccess && g &&
+                 cudaGraphInstantiate(&ctx->graph, g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+        }
+        if (!ok) {
+            cudaGetLastError();
+            ctx->graph = nullptr;
+            ctx->graph_failed = true;
+            ctx->err.clear();
+        }
+    }
     for (int q = 0; q < n_iter; ++q) {
-        qr_status s = run_rows(ctx, 0, ctx->N);
-        if (s != QR_OK) return s;
+        if (ctx->graph && !ctx->profiling) {
+            QR_CU(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+        } else {
+            qr_status s = run_rows(ctx, 0, ctx->N);
+            if (s != QR_OK) return s;
+        }
         ctx->stats.iterations++;
     }
     const long long nonfinite_before = ctx->stats.nonfinite;
@@ -628,6 +658,7 @@ qr_status qr_picard_step(qr_ctx* ctx, int n_iter, double* residual_out)
 qr_status qr_backward_sweep(qr_ctx* ctx)
 {
     if (!ready(ctx)) return QR_EINVAL;
+    QR_CU(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
     for (int i = ctx->N - 1; i >= 0; --i) {
         qr_status s = run_rows(ctx, i, i + 1);
         if (s != QR_OK) return s;
