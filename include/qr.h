@@ -181,6 +181,12 @@ const char* qr_last_error(const qr_ctx* ctx);
 const char* qr_status_string(qr_status s);
 void qr_destroy(qr_ctx* ctx);
 
+/* n test points of time index i, nu-distributed and independent of the
+ * clouds (Philox tag 2, counter (p, c, 0xffffffff, ...)): x_out is n*d
+ * doubles, host. They serve the accuracy reports of Sec. 5, eq. (mse):
+ * MSE over 10^3 nu-points per time index. */
+qr_status qr_test_points(const qr_ctx* ctx, int i, long long n, double* x_out);
+
 /* ---- test hooks (no context) ------------------------------------------ */
 
 /* Philox4x32-10 on the device: ctr_key is n rows of 6 words (ctr0..3, key0,1),

@@ -25,7 +25,7 @@ QR_HOST, QR_DEVICE = 0, 1
 EXPORTS = [
     "qr_init", "qr_picard_step", "qr_backward_sweep", "qr_eval", "qr_gamma_size", "qr_gamma_list",
     "qr_get_coefs", "qr_set_coefs", "qr_get_responses", "qr_set_profiling", "qr_get_stats",
-    "qr_last_error", "qr_status_string", "qr_destroy", "qr_philox_words", "qr_sample", "qr_project_static",
+    "qr_last_error", "qr_status_string", "qr_destroy", "qr_philox_words", "qr_sample", "qr_project_static", "qr_test_points",
 ]
 
 
@@ -123,6 +123,8 @@ def load(path: str | None = None):
     L.qr_sample.restype = C.c_int
     L.qr_sample.argtypes = [C.c_int, C.POINTER(QrNu), C.c_ulonglong, C.c_int, C.c_int, C.c_longlong, C.c_longlong,
                             C.c_int, C.c_int, dp, dp, dp]
+    L.qr_test_points.restype = C.c_int
+    L.qr_test_points.argtypes = [vp, C.c_int, C.c_longlong, dp]
     L.qr_project_static.restype = C.c_int
     L.qr_project_static.argtypes = [vp, vp, C.c_int, C.c_int, vp]
     _lib = L

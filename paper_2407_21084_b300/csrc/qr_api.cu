@@ -772,6 +772,22 @@ qr_status qr_get_stats(const qr_ctx* ctx, qr_stats_t* out)
     return QR_OK;
 }
 
+qr_status qr_test_points(const qr_ctx* ctx, int i, long long n, double* x_out)
+{
+    if (!ready(ctx) || !x_out || n < 0 || i < 0 || i > ctx->N) return QR_EINVAL;
+    if (n == 0) return QR_OK;
+    qr_ctx* c = const_cast<qr_ctx*>(ctx);
+    double* d = nullptr;
+    QR_CU(c, cudaMallocAsync(&d, sizeof(double) * (size_t)n * ctx->d, ctx->stream));
+    cudaError_t e = launch_test_points(ctx->P, i, n, d, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(x_out, d, sizeof(double) * (size_t)n * ctx->d, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaFreeAsync(d, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "test points");
+    return QR_OK;
+}
+
 qr_status qr_philox_words(const uint32_t* ctr_key, long long n, uint32_t* out)
 {
     if (n < 0 || (n > 0 && (!ctr_key || !out))) return QR_EINVAL;

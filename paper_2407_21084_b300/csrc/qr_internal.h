@@ -65,6 +65,7 @@ cudaError_t launch_pack(int prec, const QrParams& P, const double2* alpha, int n
 cudaError_t launch_eval(int prec, const QrParams& P, const GEntry* tab, const uint8_t* first,
                         const void* packed_row, const double* x, long long n, double* y, int use_g,
                         cudaStream_t st);
+cudaError_t launch_test_points(const QrParams& P, int i, long long n, double* x, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr_key, long long n, uint32_t* out, cudaStream_t st);
 cudaError_t launch_sample(int prec, const QrParams& P, int i, long long m0, long long n, int j,
                           double* u, double* x, double* z, cudaStream_t st);

@@ -440,6 +440,29 @@ __global__ void k_sample(const __grid_constant__ QrParams P, int i, long long m0
     }
 }
 
+// test points: X = F^{-1}(U), U from the TEST tag (counter j = 0xffffffff)
+template <int D>
+__global__ void k_test_points(const __grid_constant__ QrParams P, int i, long long n, double* x)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const uint2 key = make_uint2(P.key0, P.key1);
+#pragma unroll
+    for (int c = 0; 2 * c < D; ++c) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)t, (uint32_t)c, 0xffffffffu, ctr_hi(P.instance, QR_TAG_TEST, i)), key);
+        x[t * D + 2 * c] = nu_icdf<double>(P, u52(r.x, r.y));
+        if (2 * c + 1 < D) x[t * D + 2 * c + 1] = nu_icdf<double>(P, u52(r.z, r.w));
+    }
+}
+
+template <int D>
+static cudaError_t test_points_t(const QrParams& P, int i, long long n, double* x, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_test_points<D><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(P, i, n, x);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ launchers
 constexpr int kBS32 = 256, kBS64 = 128;
 
@@ -587,6 +610,21 @@ cudaError_t launch_eval(int prec, const QrParams& P, const GEntry* tab, const ui
         QR_DISPATCH_D(eval_t, float, P, tab, first, packed_row, x, n, y, use_g, st)
     }
     QR_DISPATCH_D(eval_t, double, P, tab, first, packed_row, x, n, y, use_g, st)
+}
+
+cudaError_t launch_test_points(const QrParams& P, int i, long long n, double* x, cudaStream_t st)
+{
+    switch (P.d) {
+    case 1: return test_points_t<1>(P, i, n, x, st);
+    case 2: return test_points_t<2>(P, i, n, x, st);
+    case 3: return test_points_t<3>(P, i, n, x, st);
+    case 4: return test_points_t<4>(P, i, n, x, st);
+    case 5: return test_points_t<5>(P, i, n, x, st);
+    case 6: return test_points_t<6>(P, i, n, x, st);
+    case 7: return test_points_t<7>(P, i, n, x, st);
+    case 8: return test_points_t<8>(P, i, n, x, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_philox(const uint32_t* ctr_key, long long n, uint32_t* out, cudaStream_t st)

@@ -112,6 +112,23 @@ class Solver:
                                 L.QR_HOST), self._ctx)
         return y
 
+    def test_points(self, i: int, n: int) -> np.ndarray:
+        """n nu-distributed test points of time index i (Philox test tag), shape (n, d)."""
+        x = np.zeros((n, self.d))
+        L.check(self._L.qr_test_points(self._ctx, i, n, _dp(x)), self._ctx)
+        return x
+
+    def mse_indicators(self, exact, n: int = 1000) -> dict:
+        """MSE_max and MSE_av of Sec. 5, eq. (mse): natural logs of the mean
+        squared error of ybar_i against exact(t_i, x) at n test points per i."""
+        per_i = []
+        for i in range(self.N):
+            x = self.test_points(i, n)
+            e = self.eval(i, x) - exact(i * self.T / self.N, x)
+            per_i.append(float(np.mean(e * e)))
+        per_i = np.array(per_i)
+        return {"mse_max": float(np.log(per_i.max())), "mse_av": float(np.log(per_i.mean())), "points": n}
+
     def set_profiling(self, on: bool = True):
         L.check(self._L.qr_set_profiling(self._ctx, 1 if on else 0), self._ctx)
 

@@ -232,3 +232,13 @@ def test_tree_and_table_kernels_agree_on_c3_prefix(qr):
             s.picard_step(2)
             a.append(s.coefs())
     assert relerr(a[0], a[1]) < 1e-5
+
+
+def test_test_points_match_oracle(qr, ora):
+    w = W.c2()
+    p = ora_problem(ora, w, M=64)
+    with _solver(qr, w, FP64, M=64) as s:
+        for i in (0, 7):
+            x = s.test_points(i, 257)
+            xo = ora.test_points(p, i, 257)
+            assert np.all(np.abs(x - xo) <= 1e-14 * (1 + np.abs(xo)))
