@@ -187,6 +187,33 @@ void qr_destroy(qr_ctx* ctx);
  * MSE over 10^3 nu-points per time index. */
 qr_status qr_test_points(const qr_ctx* ctx, int i, long long n, double* x_out);
 
+/* ---- learned warm start (no counterpart in the paper's algorithm) -------
+ * A multilayer perceptron y = W_L(...gelu(x W_1 + b_1)...) + b_L with `depth`
+ * hidden layers of `width` units (GELU, erf form) maps a row of inputs (for
+ * the benchmark family: the wave vector s, sigma0, a and t_i) to a
+ * coefficient row alpha_i (|Gamma| reals: alpha_0 and (re, im) of the half
+ * set), used as the Picard iteration's start in place of y == 0. Training
+ * is plain Adam on the mean squared error, in FP32, with the library's own
+ * kernels (tiled GEMM with fused bias/GELU, GELU backward, Adam).
+ * Buffers X (B x n_in), T and Y (B x n_out) are row-major FP32 device
+ * arrays of the caller; B <= max_batch. Parameters are one flat FP32 array:
+ * for each layer W (n_in x n_out, row-major) then b. Every call returns a
+ * qr_status; qr_mlp_last_error gives text. */
+typedef struct qr_mlp qr_mlp;
+qr_status qr_mlp_create(qr_mlp** out, int n_in, int width, int depth, int n_out, int max_batch,
+                        unsigned long long seed, void* stream);
+long long qr_mlp_num_params(const qr_mlp* m);
+qr_status qr_mlp_get_params(const qr_mlp* m, float* out /* host, num_params */);
+qr_status qr_mlp_set_params(qr_mlp* m, const float* in /* host, num_params */);
+qr_status qr_mlp_forward(qr_mlp* m, const float* X, int B, float* Y);
+/* gradient of mean((Y - T)^2) with respect to the parameters (host array
+ * grad_out, nullable) and the loss (host, nullable); parameters unchanged */
+qr_status qr_mlp_gradients(qr_mlp* m, const float* X, const float* T, int B, float* grad_out, float* loss_out);
+/* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on a batch */
+qr_status qr_mlp_train_step(qr_mlp* m, const float* X, const float* T, int B, float lr, float* loss_out);
+const char* qr_mlp_last_error(const qr_mlp* m);
+void qr_mlp_destroy(qr_mlp* m);
+
 /* ---- test hooks (no context) ------------------------------------------ */
 
 /* Philox4x32-10 on the device: ctr_key is n rows of 6 words (ctr0..3, key0,1),

@@ -26,6 +26,8 @@ EXPORTS = [
     "qr_init", "qr_picard_step", "qr_backward_sweep", "qr_eval", "qr_gamma_size", "qr_gamma_list",
     "qr_get_coefs", "qr_set_coefs", "qr_get_responses", "qr_set_profiling", "qr_get_stats",
     "qr_last_error", "qr_status_string", "qr_destroy", "qr_philox_words", "qr_sample", "qr_project_static", "qr_test_points",
+    "qr_mlp_create", "qr_mlp_num_params", "qr_mlp_get_params", "qr_mlp_set_params", "qr_mlp_forward",
+    "qr_mlp_gradients", "qr_mlp_train_step", "qr_mlp_last_error", "qr_mlp_destroy",
 ]
 
 
@@ -123,6 +125,25 @@ def load(path: str | None = None):
     L.qr_sample.restype = C.c_int
     L.qr_sample.argtypes = [C.c_int, C.POINTER(QrNu), C.c_ulonglong, C.c_int, C.c_int, C.c_longlong, C.c_longlong,
                             C.c_int, C.c_int, dp, dp, dp]
+    fp = C.POINTER(C.c_float)
+    L.qr_mlp_create.restype = C.c_int
+    L.qr_mlp_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_ulonglong, vp]
+    L.qr_mlp_num_params.restype = C.c_longlong
+    L.qr_mlp_num_params.argtypes = [vp]
+    L.qr_mlp_get_params.restype = C.c_int
+    L.qr_mlp_get_params.argtypes = [vp, fp]
+    L.qr_mlp_set_params.restype = C.c_int
+    L.qr_mlp_set_params.argtypes = [vp, fp]
+    L.qr_mlp_forward.restype = C.c_int
+    L.qr_mlp_forward.argtypes = [vp, vp, C.c_int, vp]
+    L.qr_mlp_gradients.restype = C.c_int
+    L.qr_mlp_gradients.argtypes = [vp, vp, vp, C.c_int, fp, fp]
+    L.qr_mlp_train_step.restype = C.c_int
+    L.qr_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, fp]
+    L.qr_mlp_last_error.restype = C.c_char_p
+    L.qr_mlp_last_error.argtypes = [vp]
+    L.qr_mlp_destroy.restype = None
+    L.qr_mlp_destroy.argtypes = [vp]
     L.qr_test_points.restype = C.c_int
     L.qr_test_points.argtypes = [vp, C.c_int, C.c_longlong, dp]
     L.qr_project_static.restype = C.c_int
