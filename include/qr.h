@@ -187,6 +187,26 @@ void qr_destroy(qr_ctx* ctx);
  * MSE over 10^3 nu-points per time index. */
 qr_status qr_test_points(const qr_ctx* ctx, int i, long long n, double* x_out);
 
+/* ---- many instances in one iteration ----------------------------------
+ * A batch advances n contexts (created by qr_init with QR_FP32, sharing one
+ * stream, each with one of the compiled index-set classes: |k|_inf <= 4 in
+ * d = 2; |k|_1 <= 5 (d = 3), 4 (d = 4, 5, 6), 3 (d = 6, 7, 8)) by Picard
+ * iterations together. The path-and-series phase of all instances is one
+ * persistent kernel launch pulling (instance, time index, path tiles) work
+ * items longest-first; projection and reduction follow per instance; one
+ * iteration is one CUDA graph launch. The first qr_batch_picard_step times a
+ * few item sizes and grids and keeps the fastest (autotuning). The batch
+ * does not own the contexts: destroy it before them. Results per instance
+ * are read with qr_get_coefs etc. max_residual (nullable): the largest
+ * residual over the instances. */
+typedef struct qr_batch qr_batch;
+qr_status qr_batch_create(qr_batch** out, qr_ctx* const* ctxs, int n);
+qr_status qr_batch_picard_step(qr_batch* b, int n_iter, double* max_residual);
+/* the autotuned choice and the timings of the candidates (6 doubles, ms) */
+qr_status qr_batch_info(const qr_batch* b, int* tiles_per_item, int* grid, double* tune_ms);
+const char* qr_batch_last_error(const qr_batch* b);
+void qr_batch_destroy(qr_batch* b);
+
 /* ---- learned warm start (no counterpart in the paper's algorithm) -------
  * A multilayer perceptron y = W_L(...gelu(x W_1 + b_1)...) + b_L with `depth`
  * hidden layers of `width` units (GELU, erf form) maps a row of inputs (for

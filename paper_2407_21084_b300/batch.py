@@ -1,0 +1,104 @@
+"""Many QRMC problem instances advanced together (qr_batch_*).
+
+    python -m paper_2407_21084_b300.batch [--instances 256] [--iters 3]
+
+runs the multi-instance workload (workloads.c4) and prints one JSON line
+with seconds per batch iteration, path.coef evaluations per second, the
+autotuner's choice and a check that a few instances match their
+single-instance runs.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import time
+
+import numpy as np
+
+from . import _lib as L
+from . import workloads as W
+from .solver import Solver
+
+
+class Batch:
+    def __init__(self, solvers):
+        self._L = L.load()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s._ctx.value for s in self.solvers])
+        self._b = C.c_void_p()
+        st = self._L.qr_batch_create(C.byref(self._b), arr, len(self.solvers))
+        if st != L.QR_OK:
+            msg = self._L.qr_batch_last_error(self._b).decode() if self._b else ""
+            self.close()
+            raise L.QrError(st, msg)
+
+    def picard_step(self, n_iter: int = 1) -> float:
+        r = C.c_double()
+        st = self._L.qr_batch_picard_step(self._b, n_iter, C.byref(r))
+        if st != L.QR_OK:
+            raise L.QrError(st, self._L.qr_batch_last_error(self._b).decode())
+        return r.value
+
+    def info(self) -> dict:
+        tpi, grid = C.c_int(), C.c_int()
+        ms = (C.c_double * 6)()
+        self._L.qr_batch_info(self._b, C.byref(tpi), C.byref(grid), ms)
+        return {"tiles_per_item": tpi.value, "grid": grid.value, "tune_ms": list(ms)}
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._L.qr_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def solvers_for(ws, stream):
+    return [Solver.from_workload(w, precision=L.QR_FP32, stream=stream) for w in ws]
+
+
+def main():
+    import torch
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--shared", type=int, default=64)
+    ap.add_argument("--paths", type=int, default=2 ** 18)
+    ap.add_argument("--iters", type=int, default=3)
+    args = ap.parse_args()
+    ws = W.c4(args.instances, args.shared, args.paths)
+    st = torch.cuda.Stream()
+    sol = solvers_for(ws, st.cuda_stream)
+    b = Batch(sol)
+    b.picard_step(1)  # autotune + first iteration
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    b.picard_step(args.iters)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.iters
+    evals = sum(w.evals_per_iter() for w in ws)
+    # cross-check: three instances rerun alone give the same coefficients
+    same = []
+    for q in (0, len(ws) // 2, len(ws) - 1):
+        with Solver.from_workload(ws[q], precision=L.QR_FP32, stream=st.cuda_stream) as s:
+            s.picard_step(1 + args.iters)
+            same.append(bool(np.array_equal(s.coefs().view(np.float64), sol[q].coefs().view(np.float64))))
+    print(json.dumps({"workload": "c4_%d_instances" % len(ws), "instances": len(ws), "paths": args.paths,
+                      "s_per_batch_iteration": ms / 1e3, "path_coef_evals_per_s": evals / (ms / 1e3),
+                      "evals_per_iteration": evals, "autotune": b.info(), "matches_single_runs": same,
+                      "dims": sorted(set(w.d for w in ws)),
+                      "n_gamma_range": [min(w.n_gamma() for w in ws), max(w.n_gamma() for w in ws)]}))
+    b.close()
+    for s in sol:
+        s.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "qr_batch.h"
 #include "qr_fast.h"
 #include "qr_internal.h"
 
@@ -841,6 +842,249 @@ qr_status qr_sample(int d, const qr_nu* nu, unsigned long long seed, int instanc
         s = QR_ECUDA;
     cudaFree(buf);
     return s;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+struct qr_batch {
+    std::vector<qr_ctx*> ctx;
+    cudaStream_t stream = nullptr;
+    BatchInst* d_inst = nullptr;
+    BatchItem* d_items = nullptr;
+    unsigned* d_next = nullptr;
+    int n_items = 0;
+    size_t max_rowbytes = 0;
+    int grid = 0, tiles_per_item = 1;
+    bool tuned = false;
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev[2] = {};
+    double tune_ms[8] = {};
+    std::string err;
+};
+
+namespace {
+
+qr_status bfail(qr_batch* b, qr_status s, const std::string& m)
+{
+    if (b) b->err = m;
+    return s;
+}
+
+// items of all instances, longest rows first, `tpi` tiles per item
+std::vector<BatchItem> batch_items(const qr_batch* b, int tpi)
+{
+    const int tp = batch_tile_paths();
+    std::vector<BatchItem> items;
+    for (int q = 0; q < (int)b->ctx.size(); ++q) {
+        const qr_ctx* c = b->ctx[q];
+        const int tiles = (int)((c->P.M + tp - 1) / tp);
+        for (int i = 0; i < c->N; ++i)
+            for (int t = 0; t < tiles; t += tpi) items.push_back(BatchItem{q, i, t, std::min(tpi, tiles - t)});
+    }
+    std::stable_sort(items.begin(), items.end(), [&](const BatchItem& x, const BatchItem& y) {
+        return b->ctx[x.inst]->N - x.i > b->ctx[y.inst]->N - y.i;
+    });
+    return items;
+}
+
+qr_status batch_set_items(qr_batch* b, int tpi)
+{
+    std::vector<BatchItem> items = batch_items(b, tpi);
+    if (b->d_items) cudaFree(b->d_items);
+    b->d_items = nullptr;
+    if (cudaMalloc(&b->d_items, sizeof(BatchItem) * std::max<size_t>(1, items.size())) != cudaSuccess)
+        return bfail(b, QR_ENOMEM, "batch items");
+    if (cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bfail(b, QR_ECUDA, "copy batch items");
+    b->n_items = (int)items.size();
+    b->tiles_per_item = tpi;
+    return QR_OK;
+}
+
+qr_status batch_paths(qr_batch* b)
+{
+    cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(unsigned), b->stream);
+    if (e == cudaSuccess)
+        e = launch_paths_batch(b->d_inst, b->d_items, b->n_items, b->d_next, b->max_rowbytes, b->grid, b->stream);
+    return e == cudaSuccess ? QR_OK : bfail(b, QR_ECUDA, std::string("batch path kernel: ") + cudaGetErrorString(e));
+}
+
+// projection, reduction and repack of every instance (single-instance kernels)
+qr_status batch_rest(qr_batch* b)
+{
+    for (qr_ctx* c : b->ctx) {
+        cudaError_t e = cudaMemsetAsync(c->d_counters + CNT_RESID, 0, sizeof(unsigned long long), b->stream);
+        if (e == cudaSuccess)
+            e = c->proj_nodes ? launch_project_tree(c->prec, c->gkind, c->gn, c->P, c->d_S, c->d_perm, c->d_partial,
+                                                    0, c->N, b->stream)
+                              : launch_project(c->prec, c->P, c->d_tab, c->d_first, c->d_S, c->d_partial, 0, c->N,
+                                               b->stream);
+        if (e == cudaSuccess)
+            e = launch_reduce(c->prec, c->P, c->d_partial, c->d_alpha, c->nG, c->zero_idx, c->d_packed,
+                              c->row_stride, 0, c->N, c->d_counters, b->stream);
+        if (e == cudaSuccess)
+            e = launch_pack_tree(c->prec, c->d_alpha, c->nG, c->d_tmap, c->tree_slots, c->d_tree, c->tree_stride,
+                                 c->N, b->stream);
+        if (e != cudaSuccess) return bfail(b, QR_ECUDA, std::string("batch projection: ") + cudaGetErrorString(e));
+    }
+    return QR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qr_status qr_batch_create(qr_batch** out, qr_ctx* const* ctxs, int n)
+{
+    if (!out || !ctxs || n < 1) return QR_EINVAL;
+    *out = nullptr;
+    qr_batch* b = new (std::nothrow) qr_batch();
+    if (!b) return QR_ENOMEM;
+    *out = b;
+    size_t maxrow = 16;
+    std::vector<BatchInst> inst(n);
+    for (int q = 0; q < n; ++q) {
+        qr_ctx* c = ctxs[q];
+        if (!ready(c)) return bfail(b, QR_EINVAL, "batch: instance " + std::to_string(q) + " is not a context");
+        if (c->prec != QR_FP32) return bfail(b, QR_EINVAL, "batch: instances must use QR_FP32");
+        const int cls = batch_class(c->gkind, c->d, c->gn);
+        if (cls < 0 || !c->tree_slots)
+            return bfail(b, QR_ENOTIMPL, "batch: index set of instance " + std::to_string(q) + " has no compiled class");
+        if (q > 0 && c->stream != ctxs[0]->stream) return bfail(b, QR_EINVAL, "batch: instances must share a stream");
+        b->ctx.push_back(c);
+        inst[q].P = c->P;
+        inst[q].cls = cls;
+        inst[q].tree = c->d_tree;
+        inst[q].tree_stride = c->tree_stride;
+        inst[q].S = c->d_S;
+        inst[q].counters = c->d_counters;
+        inst[q].status = c->d_status;
+        maxrow = std::max(maxrow, (size_t)c->tree_stride * sizeof(float2));
+    }
+    b->stream = ctxs[0]->stream;
+    b->max_rowbytes = (maxrow + 15) & ~size_t(15);
+    if (cudaMalloc(&b->d_inst, sizeof(BatchInst) * n) != cudaSuccess ||
+        cudaMalloc(&b->d_next, sizeof(unsigned)) != cudaSuccess)
+        return bfail(b, QR_ENOMEM, "batch allocation");
+    if (cudaMemcpy(b->d_inst, inst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bfail(b, QR_ECUDA, "copy batch instances");
+    for (auto& e : b->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return bfail(b, QR_ECUDA, "events");
+    const int per_sm = batch_blocks_per_sm(b->max_rowbytes);
+    if (per_sm < 1) return bfail(b, QR_ENOTIMPL, "batch: rows too large for shared memory");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->grid = per_sm * sms;
+    return batch_set_items(b, 4);
+}
+
+qr_status qr_batch_picard_step(qr_batch* b, int n_iter, double* max_residual)
+{
+    if (!b || b->ctx.empty() || !b->d_inst || n_iter < 0) return QR_EINVAL;
+    for (qr_ctx* c : b->ctx)
+        if (cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), b->stream) != cudaSuccess)
+            return bfail(b, QR_ECUDA, "reset status");
+    if (!b->tuned && n_iter > 0) {
+        // autotuner: time the persistent kernel for a few item sizes and
+        // grids on the first iteration (it only rewrites the responses)
+        const int tpis[] = {1, 4, 16};
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int per_sm = batch_blocks_per_sm(b->max_rowbytes);
+        const int grids[] = {per_sm * sms, std::max(1, per_sm - 1) * sms};
+        float best = 1e30f;
+        int best_t = 4, best_g = b->grid, k = 0;
+        for (int tpi : tpis)
+            for (int g : grids) {
+                qr_status s = batch_set_items(b, tpi);
+                if (s != QR_OK) return s;
+                b->grid = g;
+                cudaEventRecord(b->ev[0], b->stream);
+                s = batch_paths(b);
+                if (s != QR_OK) return s;
+                cudaEventRecord(b->ev[1], b->stream);
+                float ms = 0.f;
+                if (cudaEventSynchronize(b->ev[1]) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) != cudaSuccess)
+                    return bfail(b, QR_ECUDA, "autotune timing");
+                if (k < 8) b->tune_ms[k++] = ms;
+                if (ms < best) best = ms, best_t = tpi, best_g = g;
+            }
+        qr_status s = batch_set_items(b, best_t);
+        if (s != QR_OK) return s;
+        b->grid = best_g;
+        for (qr_ctx* c : b->ctx)
+            cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * CNT_N, b->stream);
+        b->tuned = true;
+        // capture one iteration
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            qr_status s1 = batch_paths(b), s2 = s1 == QR_OK ? batch_rest(b) : s1;
+            ok = cudaStreamEndCapture(b->stream, &g) == cudaSuccess && s2 == QR_OK && g &&
+                 cudaGraphInstantiate(&b->graph, g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+        }
+        if (!ok) {
+            cudaGetLastError();
+            b->graph = nullptr;
+            b->err.clear();
+        }
+    }
+    for (int q = 0; q < n_iter; ++q) {
+        if (b->graph) {
+            if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return bfail(b, QR_ECUDA, "graph launch");
+        } else {
+            qr_status s = batch_paths(b);
+            if (s == QR_OK) s = batch_rest(b);
+            if (s != QR_OK) return s;
+        }
+    }
+    double rmax = 0.0;
+    qr_status worst = QR_OK;
+    for (qr_ctx* c : b->ctx) {
+        if (n_iter > 0) c->stats.iterations += n_iter;
+        const long long before = c->stats.nonfinite;
+        qr_status s = check_device_status(c);
+        if (s != QR_OK) {
+            b->err = c->err;
+            worst = s;
+            continue;
+        }
+        if (c->stats.nonfinite > before) worst = QR_ENONFINITE;
+        double r;
+        std::memcpy(&r, &c->h_counters[CNT_RESID], sizeof r);
+        rmax = std::max(rmax, r);
+    }
+    if (max_residual) *max_residual = n_iter > 0 ? rmax : 0.0;
+    return worst;
+}
+
+qr_status qr_batch_info(const qr_batch* b, int* tiles_per_item, int* grid, double* tune_ms /* 6 values */)
+{
+    if (!b) return QR_EINVAL;
+    if (tiles_per_item) *tiles_per_item = b->tiles_per_item;
+    if (grid) *grid = b->grid;
+    if (tune_ms)
+        for (int k = 0; k < 6; ++k) tune_ms[k] = b->tune_ms[k];
+    return QR_OK;
+}
+
+const char* qr_batch_last_error(const qr_batch* b) { return b ? b->err.c_str() : "no batch"; }
+
+void qr_batch_destroy(qr_batch* b)
+{
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->d_inst) cudaFree(b->d_inst);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_next) cudaFree(b->d_next);
+    for (auto& e : b->ev)
+        if (e) cudaEventDestroy(e);
+    delete b;
 }
 
 }  // extern "C"

@@ -27,4 +27,13 @@ int proj_tree_nodes(int kind, int d, int n);
 cudaError_t launch_project_tree(int prec, int kind, int n, const QrParams& P, const void* S, const int* perm,
                                 double2* partial, int i_lo, int i_hi, cudaStream_t st);
 
+// further sets (qr_fast_more.cu, qr_proj_more.cu), reached through the dispatchers above
+int tree_slots_more(int kind, int d, int n);
+cudaError_t launch_paths_tree_more(int prec, int kind, int n, const QrParams& P, const void* tree,
+                                   long long row_stride, void* S, int i_lo, int i_hi, unsigned long long* counters,
+                                   unsigned* status, cudaStream_t st);
+int proj_tree_nodes_more(int kind, int d, int n);
+cudaError_t launch_project_tree_more(int prec, int kind, int n, const QrParams& P, const void* S, const int* perm,
+                                     double2* partial, int i_lo, int i_hi, cudaStream_t st);
+
 }  // namespace qr

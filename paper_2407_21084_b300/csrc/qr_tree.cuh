@@ -1,0 +1,490 @@
+// qr_tree.cuh -- compile-time chain tree of the |k|_1 <= n and |k|_inf <= n
+// half sets and the per-tile body of the path-and-series kernel; used by the
+// single-problem kernel (qr_fast.cu) and the multi-instance engine
+// (qr_batch.cu).
+#pragma once
+
+#include "qr_device.cuh"
+#include "qr_fast.h"
+
+namespace qr {
+
+template <int D, int NN, int KIND>
+struct TreeShape {
+    static constexpr bool ext_ok(int S) { return KIND == QR_G_L1 ? S >= 1 : S < NN; }
+    static constexpr int ext_S(int S) { return KIND == QR_G_L1 ? S - 1 : S + 1; }
+    static constexpr bool new_ok(int S) { return KIND == QR_G_L1 ? S >= 1 : true; }
+    static constexpr int new_S(int S) { return KIND == QR_G_L1 ? S - 1 : 1; }
+    static constexpr bool leaf(int L, int S) { return KIND == QR_G_L1 ? S == 0 : (S == NN && L == D - 1); }
+    static constexpr int root_S() { return KIND == QR_G_L1 ? NN - 1 : 1; }
+    // slots of the subtree of an internal node (L, S), its own slot included
+    static constexpr int size(int L, int S)
+    {
+        int n = 1;
+        if (ext_ok(S)) n += leaf(L, ext_S(S)) ? 1 : size(L, ext_S(S));
+        if (new_ok(S))
+            for (int l2 = L + 1; l2 < D; ++l2) n += leaf(l2, new_S(S)) ? 2 : 2 * size(l2, new_S(S));
+        return n;
+    }
+    static constexpr int total()
+    {
+        int n = 1;
+        for (int l = 0; l < D; ++l) n += leaf(l, root_S()) ? 1 : size(l, root_S());
+        return n;
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ void cfma(V2<R>& t, V2<R> c, V2<R> w)
+{
+    t.x = fma(c.x, w.x, t.x);
+    t.x = fma(-c.y, w.y, t.x);
+    t.y = fma(c.x, w.y, t.y);
+    t.y = fma(c.y, w.x, t.y);
+}
+
+// ---- per-step helpers of the tree kernel with the problem constants
+// converted once to R (no FP64 instruction per step in the FP32 form)
+template <typename R, int D>
+struct StepConsts {
+    R dt, sqdt, Lc, fc, glam, gkap, flam, fkap;
+    R b[D], sig[D * D], fs[D], gs[D];
+    bool clamp, sig_diag;
+    __device__ __forceinline__ explicit StepConsts(const QrParams& P)
+    {
+        dt = (R)P.dt;
+        sqdt = (R)P.sqdt;
+        Lc = (R)P.clamp_L;
+        clamp = P.clamp_L > 0.0;
+        fc = (R)P.f_c;
+        flam = (R)P.f_lam;
+        fkap = (R)P.f_kap;
+        glam = (R)P.g_lam;
+        gkap = (R)P.g_kap;
+        sig_diag = P.sig_diag != 0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            b[l] = (R)P.b[l];
+            fs[l] = (R)P.f_s[l];
+            gs[l] = (R)P.g_s[l];
+        }
+#pragma unroll
+        for (int t = 0; t < D * D; ++t) sig[t] = (R)P.sig[t];
+    }
+};
+
+// uniform (2n+1) 2^-53, n = (a << 20) ^ (b >> 12), from 32-bit conversions
+__device__ __forceinline__ float u01_f32(uint32_t a, uint32_t b)
+{
+    return fmaf((float)(b >> 12), 0x1p-52f, fmaf((float)a, 0x1p-32f, 0x1p-53f));
+}
+
+template <typename R, int D>
+__device__ __forceinline__ void normals_fast(const QrParams& P, int i, uint32_t m, int j, R (&z)[D])
+{
+    if constexpr (sizeof(R) == 8) {
+        normals<R, D>(P, i, m, j, z);
+    } else {
+        const uint2 key = make_uint2(P.key0, P.key1);
+#pragma unroll
+        for (int c = 0; 2 * c < D; ++c) {
+            const uint4 r = philox4x32_10(make_uint4(m, (uint32_t)c, (uint32_t)j, ctr_hi(P.instance, QR_TAG_INCR, i)), key);
+            // ln(u_a): u_a < 1/2 iff the top bit of r.x is clear; above 1/2 use log1p(-(1 - u_a)),
+            // 1 - u_a having the complemented bits
+            const float la = (r.x & 0x80000000u) ? log1pf(-u01_f32(~r.x, ~r.y)) : logf(u01_f32(r.x, r.y));
+            const float rho = sqrtf(-2.0f * la);
+            float sn, cs;
+            sincospif(2.0f * u01_f32(r.z, r.w), &sn, &cs);
+            z[2 * c] = rho * cs;
+            if (2 * c + 1 < D) z[2 * c + 1] = rho * sn;
+        }
+    }
+}
+
+template <typename R, int D>
+__device__ __forceinline__ void euler_fast(const StepConsts<R, D>& K, const R (&x)[D], const R (&z)[D], R (&x1)[D])
+{
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        R noise;
+        if (K.sig_diag) {
+            noise = K.sig[l * D + l] * z[l];
+        } else {
+            noise = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) noise += K.sig[l * D + c] * z[c];
+        }
+        x1[l] = x[l] + K.b[l] * K.dt + noise * K.sqdt;
+    }
+}
+
+template <typename R, int D>
+__device__ __forceinline__ R drv_f_fast(const QrParams& P, const StepConsts<R, D>& K, R fexp_j, const R (&x)[D], R y)
+{
+    switch (P.f_kind) {
+    case QR_F_LINEAR:
+        return K.flam * y;
+    case QR_F_CUBIC_MANUF: {
+        R sx = 0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) sx += K.fs[l] * x[l];
+        const R u = fexp_j * rcos<R>(sx);
+        return -y * y * y + (K.fc * u + u * u * u);
+    }
+    case QR_F_PAPER_MIN: {
+        R sx = 0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) sx += x[l];
+        R v = y - K.fkap - (R)1 - rsin<R>(K.flam * sx) * fexp_j;
+        v = v * v;
+        return v < (R)1 ? v : (R)1;
+    }
+    default:
+        return (R)0;
+    }
+}
+
+template <typename R, int D>
+__device__ __forceinline__ R term_g_fast(const QrParams& P, const StepConsts<R, D>& K, const R (&x)[D])
+{
+    R sx = 0;
+    if (P.g_kind == QR_GT_COS) {
+#pragma unroll
+        for (int l = 0; l < D; ++l) sx += K.gs[l] * x[l];
+        return rcos<R>(sx);
+    }
+#pragma unroll
+    for (int l = 0; l < D; ++l) sx += x[l];
+    return (R)1 + K.gkap + rsin<R>(K.glam * sx);
+}
+
+// subtrees of at most this many slots have both signs unrolled
+#ifndef QR_TREE_UNROLL
+#define QR_TREE_UNROLL 8
+#endif
+constexpr int kUnrollSlots = QR_TREE_UNROLL;
+
+template <typename R, int D, int NN, int KIND, int P, int L, int S>
+struct Node;
+
+// t += w v (complex), 4 FMA
+template <typename R>
+__device__ __forceinline__ void cmad(V2<R>& t, V2<R> w, V2<R> v)
+{
+    t.x = fma(w.x, v.x, t.x);
+    t.x = fma(-w.y, v.y, t.x);
+    t.y = fma(w.x, v.y, t.y);
+    t.y = fma(w.y, v.x, t.y);
+}
+
+// Bottom-up (Horner) evaluation: the value of the subtree of node c in its
+// own frame is V_c = coef_c + sum_children w_ch V_ch, and the series is
+// Re V_root. Every tree edge costs one complex FMA (4 FMA); a +-1 leaf pair
+// costs 4 FMA for both leaves; no prefix products are formed.
+
+// children in the new dimensions L2 .. D-1 of a node in state S
+template <typename R, int D, int NN, int KIND, int P, int L2, int S>
+struct NewDims {
+    using Sh = TreeShape<D, NN, KIND>;
+    static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, int& off, V2<R> (&T)[P],
+                                               const V2<R> (&z)[P][D])
+    {
+        if constexpr (L2 < D) {
+            constexpr int S2 = Sh::new_S(S);
+            if constexpr (Sh::leaf(L2, S2)) {
+                // T += c+ z + c- conj(z), pre-combined as (A, B), (C, E):
+                // T.x += A z.x + B z.y,  T.y += C z.y + E z.x
+                const V2<R> ab = c[off], ce = c[off + 1];
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    T[p].x = fma(ab.x, z[p][L2].x, T[p].x);
+                    T[p].x = fma(ab.y, z[p][L2].y, T[p].x);
+                    T[p].y = fma(ce.x, z[p][L2].y, T[p].y);
+                    T[p].y = fma(ce.y, z[p][L2].x, T[p].y);
+                }
+                off += 2;
+            } else {
+                constexpr int sz = Sh::size(L2, S2);
+                const V2<R>* cs = c + off;
+                if constexpr (sz <= kUnrollSlots) {
+                    // small subtrees: both signs unrolled (no loop control)
+                    V2<R> w[P], v[P];
+#pragma unroll
+                    for (int p = 0; p < P; ++p) w[p] = z[p][L2];
+                    Node<R, D, NN, KIND, P, L2, S2>::value(cs, w, z, v);
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        cmad<R>(T[p], w[p], v[p]);
+                        w[p].y = -w[p].y;
+                    }
+                    Node<R, D, NN, KIND, P, L2, S2>::value(cs + sz, w, z, v);
+#pragma unroll
+                    for (int p = 0; p < P; ++p) cmad<R>(T[p], w[p], v[p]);
+                } else {
+#pragma unroll 1
+                    for (int s = 0; s < 2; ++s) {
+                        V2<R> w[P], v[P];
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            w[p] = z[p][L2];
+                            if (s) w[p].y = -w[p].y;
+                        }
+                        Node<R, D, NN, KIND, P, L2, S2>::value(cs + s * sz, w, z, v);
+#pragma unroll
+                        for (int p = 0; p < P; ++p) cmad<R>(T[p], w[p], v[p]);
+                    }
+                }
+                off += 2 * sz;
+            }
+            NewDims<R, D, NN, KIND, P, L2 + 1, S>::run(c, off, T, z);
+        }
+    }
+};
+
+// an internal node (L, S) reached through the phase wl: its slot, then the
+// extension child (same dimension, same phase), then the new dimensions
+template <typename R, int D, int NN, int KIND, int P, int L, int S>
+struct Node {
+    using Sh = TreeShape<D, NN, KIND>;
+    static __device__ __forceinline__ void value(const V2<R>* __restrict__ c, const V2<R> (&wl)[P],
+                                                 const V2<R> (&z)[P][D], V2<R> (&T)[P])
+    {
+        const V2<R> c0 = c[0];
+#pragma unroll
+        for (int p = 0; p < P; ++p) T[p] = c0;
+        int off = 1;
+        if constexpr (Sh::ext_ok(S)) {
+            constexpr int S2 = Sh::ext_S(S);
+            if constexpr (Sh::leaf(L, S2)) {
+                const V2<R> ce = c[off];
+#pragma unroll
+                for (int p = 0; p < P; ++p) cfma<R>(T[p], ce, wl[p]);
+                off += 1;
+            } else {
+                V2<R> v[P];
+                Node<R, D, NN, KIND, P, L, S2>::value(c + off, wl, z, v);
+#pragma unroll
+                for (int p = 0; p < P; ++p) cmad<R>(T[p], wl[p], v[p]);
+                off += Sh::size(L, S2);
+            }
+        }
+        if constexpr (Sh::new_ok(S)) NewDims<R, D, NN, KIND, P, L + 1, S>::run(c, off, T, z);
+    }
+};
+
+// root children (first nonzero coordinate, sign +)
+template <typename R, int D, int NN, int KIND, int P, int L>
+struct RootKids {
+    using Sh = TreeShape<D, NN, KIND>;
+    static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, int& off, V2<R> (&T)[P],
+                                               const V2<R> (&z)[P][D])
+    {
+        if constexpr (L < D) {
+            constexpr int S0 = Sh::root_S();
+            if constexpr (Sh::leaf(L, S0)) {
+                const V2<R> ce = c[off];
+#pragma unroll
+                for (int p = 0; p < P; ++p) cfma<R>(T[p], ce, z[p][L]);
+                off += 1;
+            } else {
+                V2<R> w[P], v[P];
+#pragma unroll
+                for (int p = 0; p < P; ++p) w[p] = z[p][L];
+                Node<R, D, NN, KIND, P, L, S0>::value(c + off, w, z, v);
+#pragma unroll
+                for (int p = 0; p < P; ++p) cmad<R>(T[p], w[p], v[p]);
+                off += Sh::size(L, S0);
+            }
+            RootKids<R, D, NN, KIND, P, L + 1>::run(c, off, T, z);
+        }
+    }
+};
+
+template <typename R, int D, int NN, int KIND, int P>
+__device__ __forceinline__ void tree_series(const V2<R>* __restrict__ c, const V2<R> (&z)[P][D], R (&y)[P])
+{
+    V2<R> T[P];
+    const V2<R> c0 = c[0];
+#pragma unroll
+    for (int p = 0; p < P; ++p) T[p] = c0;
+    int off = 1;
+    RootKids<R, D, NN, KIND, P, 0>::run(c, off, T, z);
+#pragma unroll
+    for (int p = 0; p < P; ++p) y[p] = T[p].x;
+}
+
+
+// One work item of the path-and-series kernel: the tile of BS*P paths
+// starting at path m0 (this thread: m0 + p*BS) of time index i. Coefficient
+// rows i+1.. are staged into the two buffers abuf (row i+1 into abuf[0]);
+// phase[] carries the mbarrier parities across the items a CTA processes.
+// Returns false when a bounded wait ran out (the status word is set).
+template <typename R, int D, int NN, int KIND, int P, int BS>
+__device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __restrict__ tree, long long row_stride,
+                                          R* __restrict__ S, int i, int i_lo, long long m0, V2<R>* const (&abuf)[2],
+                                          uint64_t* bars, uint32_t (&phase)[2],
+                                          unsigned long long* __restrict__ counters, unsigned* __restrict__ status)
+{
+    const int tid = threadIdx.x, N = Pm.N;
+    const bool trig = Pm.g_kind == QR_GT_TRIGPOLY;
+    const uint32_t rowbytes = (uint32_t)(row_stride * sizeof(V2<R>));
+    bool inflight[2] = {false, false};
+    if (i + 1 < N || (i + 1 == N && trig)) {
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            bulk_load(abuf[0], tree + (size_t)(i + 1) * row_stride, rowbytes, &bars[0]);
+        }
+        inflight[0] = true;
+    }
+
+    const StepConsts<R, D> K(Pm);
+    R x[P][D], sum[P], comp[P], gN[P];
+    unsigned long long hits = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        V2<R> unused[D];
+        start_point<R, D>(Pm, i, m0 + p * BS, x[p], unused, false);
+        sum[p] = comp[p] = gN[p] = 0;
+    }
+    const R dt = K.dt;
+
+    for (int j = i; j < N; ++j) {
+        const int buf = (j - i) & 1, row = j + 1;
+        const bool use_series = row < N || trig;
+        const int nrow = row + 1;
+        const R fexp_j = (R)Pm.fexp[j];
+        if (nrow < N || (nrow == N && trig)) {
+            if (tid == 0) {
+                fence_proxy_async_smem();
+                bulk_load(abuf[buf ^ 1], tree + (size_t)nrow * row_stride, rowbytes, &bars[buf ^ 1]);
+            }
+            inflight[buf ^ 1] = true;
+        }
+        R x1[P][D], y[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            R z[D];
+            normals_fast<R, D>(Pm, i, (uint32_t)(m0 + p * BS), j, z);
+            euler_fast<R, D>(K, x[p], z, x1[p]);
+        }
+        if (use_series) {
+            const bool ok = mbar_wait(&bars[buf], phase[buf]);
+            phase[buf] ^= 1u;
+            inflight[buf] = false;
+            if (!__syncthreads_and(ok)) {
+                if (tid == 0) {
+                    atomicOr(status, ST_TIMEOUT);
+                    if (inflight[buf ^ 1]) (void)mbar_wait(&bars[buf ^ 1], phase[buf ^ 1]);
+                }
+                __syncthreads();
+                return false;
+            }
+            V2<R> zz[P][D];
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+#pragma unroll
+                for (int l = 0; l < D; ++l) zz[p][l] = nu_phase<R>(Pm, x1[p][l]);
+            tree_series<R, D, NN, KIND, P>(abuf[buf], zz, y);
+            if (row < N && K.clamp) {
+                const R Lc = K.Lc;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    if (y[p] > Lc) {
+                        y[p] = Lc;
+                        if (m0 + p * BS < Pm.M) ++hits;
+                    } else if (y[p] < -Lc) {
+                        y[p] = -Lc;
+                        if (m0 + p * BS < Pm.M) ++hits;
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p) y[p] = term_g_fast<R, D>(Pm, K, x1[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (row == N) gN[p] = y[p];
+            const R term = drv_f_fast<R, D>(Pm, K, fexp_j, x[p], y[p]) * dt;
+            const R yk = term - comp[p];
+            const R tk = sum[p] + yk;
+            comp[p] = (tk - sum[p]) - yk;
+            sum[p] = tk;
+#pragma unroll
+            for (int l = 0; l < D; ++l) x[p][l] = x1[p][l];
+        }
+        __syncthreads();
+    }
+    unsigned long long bad = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const long long m = m0 + p * BS;
+        if (m < Pm.M) {
+            const R Sv = gN[p] + sum[p];
+            S[(size_t)(i - i_lo) * (size_t)Pm.M + (size_t)m] = Sv;
+            if (!isfinite(Sv)) ++bad;
+        }
+    }
+    hits = warp_sum_ull(hits);
+    bad = warp_sum_ull(bad);
+    if ((tid & 31) == 0) {
+        if (hits) atomicAdd(&counters[CNT_CLAMP], hits);
+        if (bad) atomicAdd(&counters[CNT_NONFINITE], bad);
+    }
+    return true;
+}
+
+// ------------------------------------------------------ path-and-series kernel
+template <typename R, int D, int NN, int KIND, int P, int BS>
+__global__ void __launch_bounds__(BS) k_paths_tree(const __grid_constant__ QrParams P_, const V2<R>* __restrict__ tree,
+                                                   long long row_stride, R* __restrict__ S, int i_lo,
+                                                   int tiles_per_i, unsigned long long* __restrict__ counters,
+                                                   unsigned* __restrict__ status)
+{
+    const QrParams& Pm = P_;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t rowbytes = (uint32_t)(row_stride * sizeof(V2<R>));
+    V2<R>* const abuf[2] = {reinterpret_cast<V2<R>*>(smem), reinterpret_cast<V2<R>*>(smem + rowbytes)};
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * (size_t)rowbytes);
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase[2] = {0u, 0u};
+    const int i = i_lo + (int)(blockIdx.x / tiles_per_i);
+    const long long m0 = (long long)(blockIdx.x % tiles_per_i) * (BS * P) + threadIdx.x;
+    (void)path_item<R, D, NN, KIND, P, BS>(Pm, tree, row_stride, S, i, i_lo, m0, abuf, bars, phase, counters, status);
+}
+
+template <int D, int NN, int KIND>
+int tree_slots_t()
+{
+    return TreeShape<D, NN, KIND>::total();
+}
+
+template <typename R, int D, int NN, int KIND>
+inline cudaError_t paths_tree_t(const QrParams& P, const void* tree, long long row_stride, void* S, int i_lo,
+                                int i_hi, unsigned long long* counters, unsigned* status, cudaStream_t st)
+{
+#ifndef QR_TREE_P32
+#define QR_TREE_P32 2
+#endif
+    constexpr int PP = sizeof(R) == 4 ? QR_TREE_P32 : 1;  // paths per thread
+    constexpr int BS = 128;
+    const size_t sm = 2 * (size_t)row_stride * sizeof(V2<R>) + 16;
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
+    auto kern = k_paths_tree<R, D, NN, KIND, PP, BS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int tiles = (int)((P.M + BS * PP - 1) / (BS * PP));
+    const long long blocks = (long long)tiles * (i_hi - i_lo);
+    if (blocks <= 0) return cudaSuccess;
+    kern<<<(unsigned)blocks, BS, sm, st>>>(P, static_cast<const V2<R>*>(tree), row_stride, static_cast<R*>(S), i_lo,
+                                           tiles, counters, status);
+    return cudaGetLastError();
+}
+
+
+}  // namespace qr

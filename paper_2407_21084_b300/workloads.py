@@ -112,4 +112,33 @@ def c3() -> Workload:
                     gamma_n=5, M=2 ** 22, n_iter=1, a=0.2, s=_s(3, 6), seed=3)
 
 
+# index-set class per dimension for the multi-instance workload (the engine
+# compiles these classes): |Gamma| from 81 to 1289
+C4_CLASSES = {2: [(G_LINF_Z, 4)], 3: [(G_L1_Z, 5)], 4: [(G_L1_Z, 4)], 5: [(G_L1_Z, 4)],
+              6: [(G_L1_Z, 3), (G_L1_Z, 4)], 7: [(G_L1_Z, 3)], 8: [(G_L1_Z, 3)]}
+
+
+def c4(n_instances: int = 256, n_shared: int = 64, M: int = 2 ** 18, seed: int = 4) -> list:
+    """Many independent problems of uneven size: d ~ U{2..8} with the index
+    set of C4_CLASSES (|Gamma| 81..1289), N ~ U{8,16,32}, sigma0 ~ U[0.2,0.6],
+    a ~ U[0,0.5], s ~ U[-1,1]^d, M paths each. The last n_shared instances
+    share their sample points (same d, N, sigma0, index set, seed and Philox
+    instance; only a and s differ)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(n_instances - n_shared):
+        d = int(rng.integers(2, 9))
+        kind, n = C4_CLASSES[d][int(rng.integers(len(C4_CLASSES[d])))]
+        out.append(Workload("c4_inst%03d_d%d" % (q, d), d=d, N=int(rng.choice([8, 16, 32])), T=1.0,
+                            sigma0=float(rng.uniform(0.2, 0.6)), gamma_kind=kind, gamma_n=n, M=M, n_iter=1,
+                            a=float(rng.uniform(0.0, 0.5)), s=rng.uniform(-1.0, 1.0, size=d), seed=4000 + q))
+    if n_shared:
+        d, sig = 6, float(rng.uniform(0.2, 0.6))
+        for q in range(n_shared):
+            out.append(Workload("c4_shared%02d_d6" % q, d=d, N=16, T=1.0, sigma0=sig, gamma_kind=G_L1_Z, gamma_n=3,
+                                M=M, n_iter=1, a=float(rng.uniform(0.0, 0.5)), s=rng.uniform(-1.0, 1.0, size=d),
+                                seed=4999))
+    return out
+
+
 CONFIGS = {"c1": c1, "c2": c2, "c3": c3}
