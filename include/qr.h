@@ -204,6 +204,21 @@ qr_status qr_batch_create(qr_batch** out, qr_ctx* const* ctxs, int n);
 qr_status qr_batch_picard_step(qr_batch* b, int n_iter, double* max_residual);
 /* the autotuned choice and the timings of the candidates (6 doubles, ms) */
 qr_status qr_batch_info(const qr_batch* b, int* tiles_per_item, int* grid, double* tune_ms);
+/* Instances that share their sample points -- same d, N, M, sigma, b, index
+ * set, density, seed, Philox instance and start-point source, driver
+ * QR_F_CUBIC_MANUF and g = QR_GT_COS, so that only a, s and the
+ * coefficients differ -- see the same Euler paths and basis values. Sets of
+ * at least min_group such instances (default 16; 0 turns grouping off) whose
+ * index set has a compiled shared-point kernel (|k|_inf <= 4 in d = 2,
+ * |k|_1 <= 3 in d = 6; N <= 64) are run by a tensor-core kernel: the series
+ * of 32 instances at a tile of 128 points is one product Phi A with BF16
+ * hi/lo split operands and FP32 accumulation (about 2^-16 relative error per
+ * product), instead of one tree evaluation per instance. Such instances do
+ * not count clamp hits (qr_stats_t.clamp_hits stays 0 for them). Must be
+ * called before the first qr_batch_picard_step; QR_EINVAL after it. */
+qr_status qr_batch_set_grouping(qr_batch* b, int min_group);
+/* number of shared-point groups and of the instances they hold */
+qr_status qr_batch_groups(const qr_batch* b, int* n_groups, int* n_grouped);
 const char* qr_batch_last_error(const qr_batch* b);
 void qr_batch_destroy(qr_batch* b);
 

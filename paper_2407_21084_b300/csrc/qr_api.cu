@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "qr_batch.h"
+#include "qr_group.h"
 #include "qr_fast.h"
 #include "qr_internal.h"
 
@@ -847,8 +848,23 @@ qr_status qr_sample(int d, const qr_nu* nu, unsigned long long seed, int instanc
 }  // extern "C"
 
 // ------------------------------------------------------------------ batches
+// instances that share their sample points, run by the tensor-core kernel
+struct BatchGroup {
+    int kind = 0, d = 0, n = 0;
+    std::vector<int> members;
+    QrParams P{};
+    GroupInst* d_inst = nullptr;
+    void* d_apack = nullptr;
+    const int* d_perm = nullptr;
+    int nG = 0, zero_idx = 0;
+    unsigned* status = nullptr;
+};
+
 struct qr_batch {
     std::vector<qr_ctx*> ctx;
+    std::vector<BatchGroup> groups;
+    std::vector<char> grouped;  // per instance
+    int group_min = 16;
     cudaStream_t stream = nullptr;
     BatchInst* d_inst = nullptr;
     BatchItem* d_items = nullptr;
@@ -877,6 +893,7 @@ std::vector<BatchItem> batch_items(const qr_batch* b, int tpi)
     const int tp = batch_tile_paths();
     std::vector<BatchItem> items;
     for (int q = 0; q < (int)b->ctx.size(); ++q) {
+        if (b->grouped[q]) continue;
         const qr_ctx* c = b->ctx[q];
         const int tiles = (int)((c->P.M + tp - 1) / tp);
         for (int i = 0; i < c->N; ++i)
@@ -907,7 +924,98 @@ qr_status batch_paths(qr_batch* b)
     cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(unsigned), b->stream);
     if (e == cudaSuccess)
         e = launch_paths_batch(b->d_inst, b->d_items, b->n_items, b->d_next, b->max_rowbytes, b->grid, b->stream);
+    for (const BatchGroup& g : b->groups) {
+        if (e == cudaSuccess)
+            e = launch_pack_group(g.kind, g.d, g.n, g.d_inst, (int)g.members.size(), g.nG, g.zero_idx, g.d_perm,
+                                  g.d_apack, g.P.N, b->stream);
+        if (e == cudaSuccess)
+            e = launch_paths_group(g.kind, g.d, g.n, g.P, g.d_inst, (int)g.members.size(), g.d_apack, g.status,
+                                   b->stream);
+    }
     return e == cudaSuccess ? QR_OK : bfail(b, QR_ECUDA, std::string("batch path kernel: ") + cudaGetErrorString(e));
+}
+
+// same Euler paths and the same basis: every input of the path simulation
+// and of the index set agrees; the driver and g are the cubic/cosine pair
+bool shares_points(const qr_ctx* a, const qr_ctx* c)
+{
+    const QrParams &p = a->P, &q = c->P;
+    if (a->d != c->d || a->N != c->N || p.M != q.M || a->gkind != c->gkind || a->gn != c->gn) return false;
+    if (p.nu_kind != q.nu_kind || p.mu != q.mu || p.T != q.T || p.sig_diag != q.sig_diag) return false;
+    if (p.key0 != q.key0 || p.key1 != q.key1 || p.instance != q.instance || p.lattice_n != q.lattice_n) return false;
+    for (int l = 0; l < a->d; ++l)
+        if (p.b[l] != q.b[l]) return false;
+    for (int t = 0; t < kDMax * kDMax; ++t)
+        if (p.sig[t] != q.sig[t]) return false;
+    return true;
+}
+
+void free_groups(qr_batch* b)
+{
+    for (BatchGroup& g : b->groups) {
+        if (g.d_inst) cudaFree(g.d_inst);
+        if (g.d_apack) cudaFree(g.d_apack);
+    }
+    b->groups.clear();
+    b->grouped.assign(b->ctx.size(), 0);
+}
+
+// sets of at least group_min instances sharing their points (and with a
+// compiled shared-point kernel) go to the tensor-core path
+qr_status batch_build_groups(qr_batch* b)
+{
+    free_groups(b);
+    const int n = (int)b->ctx.size();
+    std::vector<char> seen(n, 0);
+    for (int q = 0; q < n && b->group_min > 0; ++q) {
+        if (seen[q]) continue;
+        const qr_ctx* c = b->ctx[q];
+        if (!group_supported(c->gkind, c->d, c->gn) || !c->d_perm || c->N > kGroupNMax) continue;
+        if (c->P.f_kind != QR_F_CUBIC_MANUF || c->P.g_kind != QR_GT_COS) continue;
+        std::vector<int> mem;
+        for (int r = q; r < n; ++r) {
+            const qr_ctx* e = b->ctx[r];
+            if (!seen[r] && e->P.f_kind == QR_F_CUBIC_MANUF && e->P.g_kind == QR_GT_COS && shares_points(c, e))
+                mem.push_back(r);
+        }
+        if ((int)mem.size() < b->group_min) continue;
+        BatchGroup g;
+        g.kind = c->gkind;
+        g.d = c->d;
+        g.n = c->gn;
+        g.members = mem;
+        g.P = c->P;
+        g.d_perm = c->d_perm;
+        g.nG = c->nG;
+        g.zero_idx = c->zero_idx;
+        g.status = c->d_status;
+        std::vector<GroupInst> gi(mem.size());
+        for (size_t t = 0; t < mem.size(); ++t) {
+            const qr_ctx* e = b->ctx[mem[t]];
+            seen[mem[t]] = 1;
+            GroupInst& I = gi[t];
+            std::memset(&I, 0, sizeof I);
+            for (int l = 0; l < e->d; ++l) {
+                I.p.fs[l] = (float)e->P.f_s[l];
+                I.p.gs[l] = (float)e->P.g_s[l];
+            }
+            I.p.f_c = (float)e->P.f_c;
+            I.p.clamp_L = (float)e->P.clamp_L;
+            for (int j = 0; j < e->N; ++j) I.fexp[j] = (float)e->P.fexp[j];
+            I.S = e->d_S;
+            I.alpha = e->d_alpha;
+        }
+        const int ntg = ((int)mem.size() + 31) / 32;
+        const size_t abytes = (size_t)c->N * ntg * 2 * (size_t)group_block_elems(g.kind, g.d, g.n) * 2;
+        const bool ok = cudaMalloc(&g.d_inst, sizeof(GroupInst) * gi.size()) == cudaSuccess &&
+                        cudaMalloc(&g.d_apack, abytes) == cudaSuccess;
+        b->groups.push_back(g);
+        if (!ok) return bfail(b, QR_ENOMEM, "batch group allocation");
+        if (cudaMemcpy(g.d_inst, gi.data(), sizeof(GroupInst) * gi.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bfail(b, QR_ECUDA, "copy group instances");
+        for (int r : mem) b->grouped[r] = 1;
+    }
+    return QR_OK;
 }
 
 // projection, reduction and repack of every instance (single-instance kernels)
@@ -977,7 +1085,28 @@ qr_status qr_batch_create(qr_batch** out, qr_ctx* const* ctxs, int n)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     b->grid = per_sm * sms;
+    qr_status gs = batch_build_groups(b);
+    if (gs != QR_OK) return gs;
     return batch_set_items(b, 4);
+}
+
+qr_status qr_batch_set_grouping(qr_batch* b, int min_group)
+{
+    if (!b || b->ctx.empty() || min_group < 0) return QR_EINVAL;
+    if (b->tuned) return bfail(b, QR_EINVAL, "batch: grouping is fixed after the first iteration");
+    b->group_min = min_group;
+    qr_status s = batch_build_groups(b);
+    return s == QR_OK ? batch_set_items(b, b->tiles_per_item) : s;
+}
+
+qr_status qr_batch_groups(const qr_batch* b, int* n_groups, int* n_grouped)
+{
+    if (!b) return QR_EINVAL;
+    int k = 0;
+    for (const BatchGroup& g : b->groups) k += (int)g.members.size();
+    if (n_groups) *n_groups = (int)b->groups.size();
+    if (n_grouped) *n_grouped = k;
+    return QR_OK;
 }
 
 qr_status qr_batch_picard_step(qr_batch* b, int n_iter, double* max_residual)
@@ -1082,6 +1211,7 @@ void qr_batch_destroy(qr_batch* b)
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_next) cudaFree(b->d_next);
+    free_groups(b);
     for (auto& e : b->ev)
         if (e) cudaEventDestroy(e);
     delete b;
