@@ -47,7 +47,13 @@ int batch_class(int kind, int d, int n)
 
 constexpr int kBatchBS = 128, kBatchP = 2;
 
-__global__ void __launch_bounds__(kBatchBS) k_paths_batch(const BatchInst* __restrict__ inst,
+// resident CTAs per SM the register allocation is held to (3: 168 registers,
+// a few hundred bytes of spills, still 17% faster than 255 registers at 2 CTAs)
+#ifndef QR_BATCH_MINB
+#define QR_BATCH_MINB 3
+#endif
+
+__global__ void __launch_bounds__(kBatchBS, QR_BATCH_MINB) k_paths_batch(const BatchInst* __restrict__ inst,
                                                           const BatchItem* __restrict__ items, int n_items,
                                                           unsigned* __restrict__ next_item, uint32_t max_rowbytes)
 {

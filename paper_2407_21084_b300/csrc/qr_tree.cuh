@@ -435,8 +435,14 @@ __device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __res
 }
 
 // ------------------------------------------------------ path-and-series kernel
+// resident CTAs per SM the register allocation is held to: 3 gives 168
+// registers and 12 warps per SM without spills for every compiled class; left
+// free, ptxas takes 255 registers (8 warps) and the d = 6 kernel runs 38% slower
+#ifndef QR_TREE_MINB
+#define QR_TREE_MINB 3
+#endif
 template <typename R, int D, int NN, int KIND, int P, int BS>
-__global__ void __launch_bounds__(BS) k_paths_tree(const __grid_constant__ QrParams P_, const V2<R>* __restrict__ tree,
+__global__ void __launch_bounds__(BS, QR_TREE_MINB) k_paths_tree(const __grid_constant__ QrParams P_, const V2<R>* __restrict__ tree,
                                                    long long row_stride, R* __restrict__ S, int i_lo,
                                                    int tiles_per_i, unsigned long long* __restrict__ counters,
                                                    unsigned* __restrict__ status)
