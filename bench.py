@@ -161,7 +161,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(W.CONFIGS))
-    ap.add_argument("--ref-paths", type=int, default=40960, help="paths of the oracle sample (about 10 s on 8 cores)")
+    ap.add_argument("--ref-paths", type=int, default=98304, help="paths of the oracle sample (10-25 s on 8-16 cores)")
     ap.add_argument("--paths", type=int, default=0, help="override M (profiling captures only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

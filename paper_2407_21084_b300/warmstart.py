@@ -225,6 +225,8 @@ def main():
     ap.add_argument("--test-points", type=int, default=1024)
     ap.add_argument("--target-scale", choices=("global", "per_output"), default="global")
     args = ap.parse_args()
+    import torch
+
     from .solver import Solver
 
     base = W.c3()
@@ -252,10 +254,19 @@ def main():
                     s.set_coefs(rows_to_alpha(net.predict(features(w))))
                 it, secs, err = iterate_to(s, pts, y_ref, args.tol, w.N + 2)
                 res[name] = {"iterations": it, "seconds": secs, "sup_error": err}
+        # Algorithm 1 itself (one backward sweep, rows in sequence) in FP32
+        with Solver.from_workload(w, precision=FP32) as s:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.backward_sweep()
+            torch.cuda.synchronize()
+            res["fp32_sweep"] = {"iterations": 1, "seconds": time.perf_counter() - t0,
+                                 "sup_error": sup_error(s, pts, y_ref)}
         rows.append(res)
     summ = {k: {"iterations_mean": float(np.mean([r[k]["iterations"] for r in rows if k in r])),
                 "seconds_mean": float(np.mean([r[k]["seconds"] for r in rows if k in r])),
-                "problems": sum(k in r for r in rows)} for k in ("fp64_cold", "fp32_cold", "fp32_warm")}
+                "problems": sum(k in r for r in rows)}
+            for k in ("fp64_cold", "fp32_cold", "fp32_warm", "fp32_sweep")}
     print(json.dumps({"train_solves": args.train, "train_paths": args.train_paths, "target_scale": args.target_scale,
                       "data_s": t_data,
                       "fit_s": t_fit, "loss_first": hist[0], "loss_last": hist[-1], "heldout": args.heldout,
