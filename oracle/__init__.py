@@ -29,6 +29,7 @@ TAG_START, TAG_INCR, TAG_TEST, TAG_PARAM = range(4)
 NU_LOMAX, NU_STUDENT2, NU_CAUCHY = range(3)
 F_ZERO, F_LINEAR, F_CUBIC_MANUF, F_PAPER_MIN = range(4)
 GT_COS, GT_TRIGPOLY, GT_PAPER_SIN = range(3)
+BASIS_FOURIER, BASIS_COS = range(2)
 
 
 def build(force: bool = False) -> str:
@@ -64,6 +65,7 @@ class _Problem(C.Structure):
         ("instance", C.c_int),
         ("clamp_L", C.c_double),
         ("lattice_n", C.c_int),
+        ("basis", C.c_int),
     ]
 
 
@@ -196,6 +198,7 @@ class Problem:
     instance: int = 0
     clamp_L: float = 0.0
     lattice_n: int = 0
+    basis: int = 0  # BASIS_FOURIER (k in Z^d) or BASIS_COS (k in N^d, real coefficients)
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> _Problem:
@@ -209,7 +212,7 @@ class Problem:
             self.d, self.N, self.T, self.nu_kind, self.mu, k.shape[0],
             k.ctypes.data_as(C.POINTER(C.c_int)), int(np.abs(k).max()) if k.size else 0,
             _dp(b), _dp(s), self.f_kind, _dp(fp), self.g_kind, _dp(gp), self.M,
-            self.seed, self.instance, self.clamp_L, self.lattice_n,
+            self.seed, self.instance, self.clamp_L, self.lattice_n, self.basis,
         )
 
     @property

@@ -9,11 +9,13 @@
  *   random start X_i^i ~ nu Sec. 2.1.2, assumption (H_nu): product density,
  *                           inverse-CDF sampling per coordinate (Sec. 5)
  *   basis                   Sec. 2.2, tensor products of 1-D functions of
- *                           F_nu(x_l) (eq. phi:dim:d, relation:1); here the
+ *                           F_nu(x_l) (eq. phi:dim:d, relation:1): either the
  *                           complex exponentials e^{2 pi i k u}, k in Z, which
  *                           are orthonormal on [0,1] exactly as the cosines
- *                           of Lemma (ortho:dim1), so that Lemma (eqInnerNorms)
- *                           makes phi_k orthonormal in L2_nu.
+ *                           of Lemma (ortho:dim1), or (basis = 1) the cosines
+ *                           C_0 = 1, C_k = sqrt(2) cos(k pi u), k in N, of
+ *                           Lemma (ortho:dim1) itself; Lemma (eqInnerNorms)
+ *                           makes phi_k orthonormal in L2_nu in both cases.
  *   response S_i            Sec. 2.3, Algorithm 1, eq. (Sqi:bar:M) with q = 0
  *   truncation T_L          Sec. 1 notation, eq. (TL:2), constant L
  *   coefficients            Sec. 2.3, Algorithm 1, eq. (Aqi:bar:M): plain
@@ -236,17 +238,31 @@ static int gamma_kmax(const ora_problem* p)
     return K;
 }
 
-/* Series at the point whose images under F_nu are u[0..d-1]. */
+/* 1-D factors of phi_k at u[0..d-1] (Sec. 2.2), E[l][v+K] for v = -K..K:
+ * e^{2 pi i v u_l} for the Fourier basis; for the cosine basis of Lemma
+ * (ortho:dim1) C_v(u_l) = 1 (v = 0), sqrt(2) cos(v pi u_l) (v > 0), real
+ * (entries with v < 0 are never used: the cosine sets lie in N^d). */
+static void factor_table(const ora_problem* p, const double* u, int K, double complex* E)
+{
+    int W = 2 * K + 1;
+    for (int l = 0; l < p->d; ++l)
+        for (int v = -K; v <= K; ++v) {
+            if (p->basis == ORA_BASIS_COS) {
+                E[l * W + v + K] = v == 0 ? 1.0 : (v > 0 ? sqrt(2.0) * cos(M_PI * (double)v * u[l]) : 0.0);
+            } else {
+                double th = 2.0 * M_PI * (double)v * u[l];
+                E[l * W + v + K] = cos(th) + I * sin(th);
+            }
+        }
+}
+
+/* Series y = Re sum_k alpha_k phi_k at the point whose images under F_nu
+ * are u[0..d-1] (for the cosine basis phi_k and alpha_k are real). */
 static double series_at_u(const ora_problem* p, const double* alpha, const double* u)
 {
     int d = p->d, K = gamma_kmax(p), W = 2 * K + 1;
-    /* E[l][v+K] = e^{2 pi i v u_l}, the 1-D factors of phi_k (Sec. 2.2). */
     double complex E[d * W];
-    for (int l = 0; l < d; ++l)
-        for (int v = -K; v <= K; ++v) {
-            double th = 2.0 * M_PI * (double)v * u[l];
-            E[l * W + v + K] = cos(th) + I * sin(th);
-        }
+    factor_table(p, u, K, E);
     double complex y = 0;
     for (int e = 0; e < p->nG; ++e) {
         double complex phi = 1.0;
@@ -383,7 +399,8 @@ static long long chunk_len(long long len)
 }
 
 /* alpha_i,k = (1/M') sum_{m in [m_lo,m_hi)} S_i^m conj(phi_k(X_i^{i,m})),
- * phi_k evaluated at the exact start uniforms (F_nu(X_i^i) = U). */
+ * phi_k evaluated at the exact start uniforms (F_nu(X_i^i) = U); for the
+ * real cosine basis conj(phi_k) = phi_k. */
 static int project_row(const ora_problem* p, const double* alpha_src, int i, long long m_lo,
                        long long m_hi, double* row_out, long long* clamp_hits)
 {
@@ -403,11 +420,7 @@ static int project_row(const ora_problem* p, const double* alpha_src, int i, lon
             long long h = 0;
             double S = ora_response(p, alpha_src, i, m, u, &h);
             hits += h;
-            for (int l = 0; l < d; ++l)
-                for (int v = -K; v <= K; ++v) {
-                    double th = 2.0 * M_PI * (double)v * u[l];
-                    E[l * W + v + K] = cos(th) + I * sin(th);
-                }
+            factor_table(p, u, K, E);
             for (int e = 0; e < nG; ++e) {
                 double complex phi = 1.0;
                 for (int l = 0; l < d; ++l) phi *= E[l * W + p->k[e * d + l] + K];

@@ -18,6 +18,10 @@
  *   ora_u01 / normals    pinned: exact bit layout, moments, KS tests.
  *   ora_nu_*             pinned: scipy's Lomax / Student-t / Cauchy laws,
  *                        density normalisation, inverse round trip, KS test.
+ *   cosine basis         pinned: planted cosine polynomial recovered exactly
+ *                        on a midpoint lattice; sampled orthonormality; the
+ *                        paper's d = 1 confidence intervals for u(0,0) = 1.6
+ *                        (Sec. 5) on its own test PDE.
  *   ora_picard_iter      pinned: planted trigonometric polynomial recovered
  *                        exactly on a lattice; the linear driver closed form;
  *                        Feynman-Kac (f=0, drift) against exact coefficients
@@ -92,6 +96,12 @@ enum {
     ORA_GT_PAPER_SIN = 2    /* g = 1+kappa+sin(lambda sum x)       par = {kappa, lambda} */
 };
 
+/* ---- basis (Sec. 2.2): tensor products of 1-D functions of u_l = F_nu(x_l) */
+enum {
+    ORA_BASIS_FOURIER = 0, /* e^{2 pi i k u}, k in Z (the benchmark workloads) */
+    ORA_BASIS_COS = 1      /* C_0 = 1, C_k = sqrt(2) cos(k pi u), k in N (Lemma ortho:dim1) */
+};
+
 typedef struct {
     int d, N;
     double T;
@@ -111,10 +121,11 @@ typedef struct {
     int instance;
     double clamp_L;      /* <= 0: no truncation */
     int lattice_n;       /* > 0: start points on the centred lattice (n^d = M) instead of Philox */
+    int basis;           /* ORA_BASIS_FOURIER (k in Z^d) or ORA_BASIS_COS (k in N^d, real alpha) */
 } ora_problem;
 
-/* Series y(x) = Re sum_{k in Gamma} alpha_k phi_k(x), phi_k(x) = prod_l e^{2 pi i k_l F(x_l)};
- * alpha: nG complex, interleaved (re, im). */
+/* Series y(x) = Re sum_{k in Gamma} alpha_k phi_k(x), phi_k(x) = prod_l e^{2 pi i k_l F(x_l)}
+ * (Fourier) or prod_l C_{k_l}(F(x_l)) (cosine); alpha: nG complex, interleaved (re, im). */
 double ora_series(const ora_problem* p, const double* alpha, const double* x);
 double ora_g(const ora_problem* p, const double* x);
 double ora_f(const ora_problem* p, double t, const double* x, double y);
