@@ -72,12 +72,29 @@ typedef struct {
     double mu;          /* used by QR_NU_LOMAX */
 } qr_nu;
 
-/* index sets of Z^d, symmetric under k -> -k (Sec. 2.4.2 lists their N^d
- * counterparts). Canonical order: lexicographic, k_1 most significant. */
+/* Index sets and basis. Kinds 0-2 are sets of Z^d, symmetric under k -> -k,
+ * with the complex Fourier basis phi_k(x) = e^{2 pi i k.F_nu(x)}. Kinds 3-5
+ * are the N^d sets of Sec. 2.4.2 with the paper's cosine basis
+ * phi_k(x) = prod_l C_{k_l}(F_nu(x_l)), C_0 = 1, C_k = sqrt(2) cos(k pi u)
+ * (Lemma ortho:dim1). A cosine context works on the unfolded set
+ * {m in Z^d : |m| in Gamma} (Gamma_F(n) -> kind 0, Gamma_T(n) -> kind 1,
+ * Gamma_H(n) -> kind 2, same n) with half-angle phases e^{i pi m.F_nu(x)}:
+ * a cosine series sum_k a_k phi_k equals Re sum_m c_m e^{i pi m.F_nu(x)} with
+ * real, sign-symmetric c_m = a_|m| 2^{-d'(m)/2}, d'(m) = #{l : m_l != 0},
+ * and after every projection the coefficients are averaged over the sign
+ * orbits, which is the cosine projection of eq. (Aqi:bar:M) in these
+ * coordinates. qr_gamma_size/list, qr_get/set_coefs and a QR_GT_TRIGPOLY g
+ * use the unfolded set and the coefficients c_m (a_k = 2^{d'(k)/2} c_k for
+ * k in N^d). Canonical order: lexicographic, k_1 most significant. The
+ * generic kernels hold per-lane power tables of d (max|k_l| + 1) complex
+ * values in shared memory; qr_init returns QR_ENOTIMPL when they exceed it. */
 enum {
     QR_G_LINF = 0,      /* max_l |k_l| <= n */
     QR_G_L1 = 1,        /* sum_l |k_l| <= n */
-    QR_G_HYP = 2        /* prod_l max(|k_l|,1) <= n */
+    QR_G_HYP = 2,       /* prod_l max(|k_l|,1) <= n */
+    QR_G_FULL_N = 3,    /* Gamma_F(n,...,n) = {k in N^d : k_l <= n}, cosine basis */
+    QR_G_TOTAL_N = 4,   /* Gamma_T(n) = {k in N^d : sum_l k_l <= n}, cosine basis */
+    QR_G_HYP_N = 5      /* Gamma_H(n) = {k in N^d : prod_l max(k_l,1) <= n}, cosine basis */
 };
 typedef struct {
     int kind;
@@ -198,7 +215,8 @@ qr_status qr_test_points(const qr_ctx* ctx, int i, long long n, double* x_out);
  * few item sizes and grids and keeps the fastest (autotuning). The batch
  * does not own the contexts: destroy it before them. Results per instance
  * are read with qr_get_coefs etc. max_residual (nullable): the largest
- * residual over the instances. */
+ * residual over the instances. Contexts of the cosine basis (kinds 3-5)
+ * are refused with QR_ENOTIMPL. */
 typedef struct qr_batch qr_batch;
 qr_status qr_batch_create(qr_batch** out, qr_ctx* const* ctxs, int n);
 qr_status qr_batch_picard_step(qr_batch* b, int n_iter, double* max_residual);
@@ -284,7 +302,8 @@ qr_status qr_sample(int d, const qr_nu* nu, unsigned long long seed, int instanc
  *              interleaved (re, im) doubles, canonical order.
  * Requires (i_hi - i_lo) * n_chunks * (|Gamma|+1)/2 <= 2^20 partial sums,
  * n_chunks = ceil(M / chunk) <= 256; otherwise returns QR_EINVAL with the
- * sizes in qr_last_error (project fewer rows per call).
+ * sizes in qr_last_error (project fewer rows per call). Contexts of the
+ * cosine basis (kinds 3-5) return QR_ENOTIMPL.
  * The call is asynchronous on the context's stream. The first call on a
  * device looks up the device address of the fixed array (once per device);
  * make that first call before any stream capture. Every call on a GPU shares

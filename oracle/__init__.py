@@ -207,6 +207,8 @@ class Problem:
         s = np.ascontiguousarray(self.sigma, dtype=np.float64).reshape(-1)
         fp = np.ascontiguousarray(np.atleast_1d(self.f_par), dtype=np.float64)
         gp = np.ascontiguousarray(np.atleast_1d(self.g_par), dtype=np.float64)
+        if k.ndim != 2 or k.shape[1] != self.d or b.size != self.d or s.size != self.d * self.d:
+            raise ValueError("k needs d columns, b d and sigma d*d entries (d = %d)" % self.d)
         self._keep = [k, b, s, fp, gp]
         return _Problem(
             self.d, self.N, self.T, self.nu_kind, self.mu, k.shape[0],

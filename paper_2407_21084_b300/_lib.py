@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libqrmc.so")
 
 QR_OK, QR_EINVAL, QR_ENOMEM, QR_ECUDA, QR_ETIMEOUT, QR_ENONFINITE, QR_ENOTIMPL = range(7)
 QR_NU_LOMAX, QR_NU_STUDENT2, QR_NU_CAUCHY = range(3)
-QR_G_LINF, QR_G_L1, QR_G_HYP = range(3)
+QR_G_LINF, QR_G_L1, QR_G_HYP, QR_G_FULL_N, QR_G_TOTAL_N, QR_G_HYP_N = range(6)
 QR_F_ZERO, QR_F_LINEAR, QR_F_CUBIC_MANUF, QR_F_PAPER_MIN = range(4)
 QR_GT_COS, QR_GT_TRIGPOLY, QR_GT_PAPER_SIN = range(3)
 QR_FP64, QR_FP32 = 0, 1

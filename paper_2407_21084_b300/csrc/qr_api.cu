@@ -1,6 +1,7 @@
 // qr_api.cu -- host side of libqrmc: argument checking, the index set Gamma,
 // the coefficient table, device state and the C-ABI of include/qr.h.
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -45,6 +46,13 @@ struct qr_ctx {
     TreeMap* d_tmap = nullptr;
     int proj_nodes = 0;  // tiled projection kernel compiled for this set
     int* d_perm = nullptr;
+    // cosine basis on N^d (Lemma ortho:dim1), run as the unfolded Z^d set
+    // with half-angle phases; raw projections are symmetrised over the sign
+    // orbits (CSR over the canonical order) after every reduction
+    bool cosine = false;
+    double2* d_alpha_raw = nullptr;
+    int* d_orb_off = nullptr;
+    int* d_orb_idx = nullptr;
     // one Picard iteration captured as a CUDA graph (built on first use when
     // profiling is off and the stream can be captured)
     cudaGraphExec_t graph = nullptr;
@@ -248,8 +256,9 @@ void release(qr_ctx* c)
 {
     if (!c) return;
     if (c->stream || c->own_stream) {
-        void* ptrs[] = {c->d_tab,     c->d_first,   c->d_alpha,    c->d_packed, c->d_S,
-                        c->d_partial, c->d_counters, c->d_status, c->d_tree,  c->d_tmap, c->d_perm};
+        void* ptrs[] = {c->d_tab,     c->d_first,   c->d_alpha,    c->d_packed,    c->d_S,
+                        c->d_partial, c->d_counters, c->d_status,   c->d_tree,      c->d_tmap,
+                        c->d_perm,    c->d_alpha_raw, c->d_orb_off, c->d_orb_idx};
         for (void* p : ptrs)
             if (p) cudaFreeAsync(p, c->stream);
         cudaStreamSynchronize(c->stream);
@@ -331,8 +340,23 @@ qr_status run_rows(qr_ctx* c, int i_lo, int i_hi)
     harvest(c, 1);
     {
         Timer t(c, 2);
-        cudaError_t e = launch_reduce(c->prec, c->P, c->d_partial, c->d_alpha, c->nG, c->zero_idx, c->d_packed,
-                                      c->row_stride, i_lo, i_hi, c->d_counters, c->stream);
+        cudaError_t e;
+        if (c->cosine) {
+            // raw projections into their own buffer (their residual goes to
+            // the spare counter slot), then the sign-orbit average into alpha
+            e = launch_reduce(c->prec, c->P, c->d_partial, c->d_alpha_raw, c->nG, c->zero_idx, c->d_packed,
+                              c->row_stride, i_lo, i_hi, c->d_counters + (CNT_SPARE - CNT_RESID), c->stream);
+            if (e == cudaSuccess)
+                e = launch_sym_cos(c->d_alpha_raw, c->d_alpha, c->nG, c->d_orb_off, c->d_orb_idx, i_lo, i_hi,
+                                   c->d_counters, c->stream);
+            if (e == cudaSuccess)
+                e = launch_pack(c->prec, c->P, c->d_alpha + (size_t)i_lo * c->nG, c->nG, c->zero_idx,
+                                static_cast<char*>(c->d_packed) + c->elem * (size_t)i_lo * c->row_stride,
+                                c->row_stride, i_hi - i_lo, c->stream);
+        } else {
+            e = launch_reduce(c->prec, c->P, c->d_partial, c->d_alpha, c->nG, c->zero_idx, c->d_packed,
+                              c->row_stride, i_lo, i_hi, c->d_counters, c->stream);
+        }
         if (e == cudaSuccess && c->tree_slots)
             e = pack_tree_rows(c, i_lo, i_hi);
         if (e != cudaSuccess) return cuda_fail(c, e, "reduction kernel");
@@ -401,8 +425,13 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     if (!nu || !gamma || !b || !sigma || !f || !g) return bail(QR_EINVAL, "null argument");
     if (nu->kind < QR_NU_LOMAX || nu->kind > QR_NU_CAUCHY) return bail(QR_EINVAL, "unknown nu kind");
     if (nu->kind == QR_NU_LOMAX && !(nu->mu > 0.0)) return bail(QR_EINVAL, "nu: mu must be positive");
-    if (gamma->kind < QR_G_LINF || gamma->kind > QR_G_HYP || gamma->n < (gamma->kind == QR_G_HYP ? 1 : 0))
+    if (gamma->kind < QR_G_LINF || gamma->kind > QR_G_HYP_N ||
+        gamma->n < ((gamma->kind == QR_G_HYP || gamma->kind == QR_G_HYP_N) ? 1 : 0))
         return bail(QR_EINVAL, "bad index set");
+    // N^d sets of the cosine basis run as their unfolding in Z^d:
+    // Gamma_F(n) -> |k|_inf <= n, Gamma_T(n) -> |k|_1 <= n, Gamma_H(n) -> prod max(|k_l|, 1) <= n
+    const bool cosine = gamma->kind >= QR_G_FULL_N;
+    const int zkind = cosine ? gamma->kind - QR_G_FULL_N : gamma->kind;
     qr_opts o{};
     o.M = 1 << 14;
     o.seed = 1;
@@ -424,13 +453,24 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     c->prec = o.precision;
 
     // index set and coefficient table
-    enumerate_gamma(gamma->kind, d, gamma->n, c->k);
+    enumerate_gamma(zkind, d, gamma->n, c->k);
+    c->cosine = cosine;
     c->nG = (int)(c->k.size() / d);
     c->zero_idx = (c->nG - 1) / 2;
     for (int l = 0; l < d; ++l)
         if (c->k[(size_t)c->zero_idx * d + l] != 0) return bail(QR_EINVAL, "index set is not symmetric");
     for (int v : c->k) c->kmax = std::max(c->kmax, v < 0 ? -v : v);
-    if (c->kmax > kKMax) return bail(QR_ENOTIMPL, "|k_l| <= 7 is required");
+    if (c->kmax > 127) return bail(QR_ENOTIMPL, "|k_l| <= 127 is required");
+    {
+        // the table kernels (generic path, projection, evaluation) keep the
+        // powers z_l^a, a <= max|k_l|, of every lane in shared memory
+        const size_t v2 = o.precision == QR_FP32 ? sizeof(float2) : sizeof(double2);
+        const size_t nGp = (size_t)(c->nG - (c->nG - 1) / 2);
+        const size_t need = (size_t)d * (c->kmax + 1) * 128 * v2 + 2 * nGp * v2 + nGp * (sizeof(GEntry) + 1) + 256;
+        if (need > 227 * 1024)
+            return bail(QR_ENOTIMPL, "index set too large for the table kernels: " + std::to_string(need / 1024) +
+                                         " KB of shared memory per block (limit 227 KB)");
+    }
     c->nGp = c->nG - c->zero_idx;
     std::vector<GEntry> tab(c->nGp);
     std::vector<uint8_t> first(c->nGp, 0);
@@ -447,6 +487,7 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     // problem parameters
     QrParams& P = c->P;
     P.d = d;
+    P.half_angle = cosine ? 1 : 0;
     P.N = N;
     P.nGp = c->nGp;
     P.K1 = c->kmax + 1;
@@ -567,12 +608,12 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     if ((s = cu(launch_pack(c->prec, P, c->d_alpha, c->nG, c->zero_idx, c->d_packed, c->row_stride, N + 1, c->stream),
                 "pack")) != QR_OK)
         return bail(s, c->err);
-    c->gkind = gamma->kind;
+    c->gkind = zkind;
     c->gn = gamma->n;
-    if (o.path_kernel == 0 && gamma->kind != QR_G_HYP) c->tree_slots = tree_slots(gamma->kind, d, gamma->n);
+    if (o.path_kernel == 0 && zkind != QR_G_HYP) c->tree_slots = tree_slots(zkind, d, gamma->n);
     if (c->tree_slots) {
         std::vector<TreeMap> map;
-        if (!build_tree_map(gamma->kind, d, gamma->n, c->k, map) || (int)map.size() != c->tree_slots)
+        if (!build_tree_map(zkind, d, gamma->n, c->k, map) || (int)map.size() != c->tree_slots)
             return bail(QR_ENOTIMPL, "tree layout does not match the compiled kernel");
         c->tree_stride = c->prec == QR_FP32 ? ((c->tree_slots + 1) & ~1) : c->tree_slots;
         if ((s = dalloc(c, &c->d_tmap, sizeof(TreeMap) * map.size())) != QR_OK) return bail(s, c->err);
@@ -585,15 +626,47 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     } else if (o.path_kernel != 0 && o.path_kernel != 1) {
         return bail(QR_EINVAL, "unknown path kernel");
     }
-    if (o.path_kernel == 0 && gamma->kind != QR_G_HYP) c->proj_nodes = proj_tree_nodes(gamma->kind, d, gamma->n);
+    if (o.path_kernel == 0 && zkind != QR_G_HYP) c->proj_nodes = proj_tree_nodes(zkind, d, gamma->n);
     if (c->proj_nodes) {
         std::vector<int> perm;
-        if (!build_proj_perm(gamma->kind, d, gamma->n, c->k, c->zero_idx, perm) || (int)perm.size() != c->proj_nodes)
+        if (!build_proj_perm(zkind, d, gamma->n, c->k, c->zero_idx, perm) || (int)perm.size() != c->proj_nodes)
             return bail(QR_ENOTIMPL, "projection order does not match the compiled kernel");
         if ((s = dalloc(c, &c->d_perm, sizeof(int) * perm.size())) != QR_OK) return bail(s, c->err);
         if ((s = cu(cudaMemcpyAsync(c->d_perm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice,
                                     c->stream),
                     "copy projection order")) != QR_OK)
+            return bail(s, c->err);
+    }
+    if (cosine) {
+        std::map<std::vector<int>, int> where;
+        for (int e = 0; e < c->nG; ++e) where[std::vector<int>(c->k.begin() + (size_t)e * d, c->k.begin() + (size_t)(e + 1) * d)] = e;
+        std::vector<int> off(1, 0), idx;
+        for (int e = 0; e < c->nG; ++e) {
+            std::vector<int> kv(c->k.begin() + (size_t)e * d, c->k.begin() + (size_t)(e + 1) * d), nz;
+            for (int l = 0; l < d; ++l)
+                if (kv[l] != 0) nz.push_back(l);
+            for (int mask = 0; mask < (1 << nz.size()); ++mask) {
+                std::vector<int> f = kv;
+                for (size_t t = 0; t < nz.size(); ++t)
+                    if (mask >> t & 1) f[nz[t]] = -f[nz[t]];
+                auto it = where.find(f);
+                if (it == where.end()) return bail(QR_EINVAL, "index set is not closed under sign flips");
+                idx.push_back(it->second);
+            }
+            off.push_back((int)idx.size());
+        }
+        if ((s = dalloc(c, &c->d_alpha_raw, sizeof(double2) * (size_t)(N + 1) * c->nG)) != QR_OK ||
+            (s = dalloc(c, &c->d_orb_off, sizeof(int) * off.size())) != QR_OK ||
+            (s = dalloc(c, &c->d_orb_idx, sizeof(int) * idx.size())) != QR_OK)
+            return bail(s, c->err);
+        if ((s = cu(cudaMemcpyAsync(c->d_orb_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice,
+                                    c->stream),
+                    "copy orbits")) != QR_OK ||
+            (s = cu(cudaMemcpyAsync(c->d_orb_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice,
+                                    c->stream),
+                    "copy orbits")) != QR_OK ||
+            (s = cu(cudaMemsetAsync(c->d_alpha_raw, 0, sizeof(double2) * (size_t)(N + 1) * c->nG, c->stream),
+                    "zero raw alpha")) != QR_OK)
             return bail(s, c->err);
     }
     if ((s = cu(cudaStreamSynchronize(c->stream), "init sync")) != QR_OK) return bail(s, c->err);
@@ -1056,6 +1129,7 @@ qr_status qr_batch_create(qr_batch** out, qr_ctx* const* ctxs, int n)
         qr_ctx* c = ctxs[q];
         if (!ready(c)) return bfail(b, QR_EINVAL, "batch: instance " + std::to_string(q) + " is not a context");
         if (c->prec != QR_FP32) return bfail(b, QR_EINVAL, "batch: instances must use QR_FP32");
+        if (c->cosine) return bfail(b, QR_ENOTIMPL, "batch: the cosine basis is not supported");
         const int cls = batch_class(c->gkind, c->d, c->gn);
         if (cls < 0 || !c->tree_slots)
             return bfail(b, QR_ENOTIMPL, "batch: index set of instance " + std::to_string(q) + " has no compiled class");

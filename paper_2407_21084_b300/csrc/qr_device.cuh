@@ -113,6 +113,8 @@ __device__ __forceinline__ R nu_icdf(const QrParams& P, uint64_t n)
 
 // e^{2 pi i F_nu(x)}: with w = F_nu(-|x|) in (0, 1/2], F = w (x < 0) or
 // 1 - w (x >= 0), so the phase is e^{+-2 pi i w} with no cancellation.
+// For the cosine basis the half angle e^{i pi F} = e^{i pi w} (x < 0) or
+// -e^{-i pi w} (x >= 0).
 template <typename R>
 __device__ __forceinline__ V2<R> nu_phase(const QrParams& P, R x)
 {
@@ -132,38 +134,44 @@ __device__ __forceinline__ V2<R> nu_phase(const QrParams& P, R x)
     } else {
         w = ((sizeof(R) == 4) ? (R)atan2f(1.0f, (float)ax) : (R)atan2(1.0, (double)ax)) * (R)0.3183098861837906715;
     }
+    // e^{2 pi i F(x)}, or e^{i pi F(x)} for the cosine basis (half angle);
+    // F(x) = w for x < 0 and 1 - w for x >= 0
+    const R ang = P.half_angle ? w : (R)2 * w;
     R s, c;
     if (sizeof(R) == 4) {
         float sf, cf;
-        sincospif(2.0f * (float)w, &sf, &cf);
+        sincospif((float)ang, &sf, &cf);
         s = sf;
         c = cf;
     } else {
         double sd, cd;
-        sincospi(2.0 * (double)w, &sd, &cd);
+        sincospi((double)ang, &sd, &cd);
         s = (R)sd;
         c = (R)cd;
     }
+    if (P.half_angle) return mk2<R>(x < (R)0 ? c : -c, s);
     return mk2<R>(c, x < (R)0 ? s : -s);
 }
 
-// e^{2 pi i u} for the exact start uniform u = (2n+1) 2^-53
+// e^{2 pi i u} (or e^{i pi u} when half) for the exact start uniform u = (2n+1) 2^-53
 template <typename R>
-__device__ __forceinline__ V2<R> u_phase(uint64_t n)
+__device__ __forceinline__ V2<R> u_phase(uint64_t n, bool half)
 {
     R w = (R)tail_odd(n) * (R)0x1p-53;  // min(u, 1-u)
+    const R ang = half ? w : (R)2 * w;
     R s, c;
     if (sizeof(R) == 4) {
         float sf, cf;
-        sincospif(2.0f * (float)w, &sf, &cf);
+        sincospif((float)ang, &sf, &cf);
         s = sf;
         c = cf;
     } else {
         double sd, cd;
-        sincospi(2.0 * (double)w, &sd, &cd);
+        sincospi((double)ang, &sd, &cd);
         s = (R)sd;
         c = (R)cd;
     }
+    if (half) return mk2<R>(n < kHalf52 ? c : -c, s);
     return mk2<R>(c, n < kHalf52 ? s : -s);
 }
 
@@ -248,7 +256,7 @@ __device__ __forceinline__ void start_point(const QrParams& P, int i, long long 
             x[l] = (R)(u < 0.5 ? -xx : xx);
             if (want_phase) {
                 double sd, cd;
-                sincospi(2.0 * u, &sd, &cd);
+                sincospi(P.half_angle ? u : 2.0 * u, &sd, &cd);
                 ph[l] = mk2<R>((R)cd, (R)sd);
             }
         }
@@ -259,7 +267,7 @@ __device__ __forceinline__ void start_point(const QrParams& P, int i, long long 
 #pragma unroll
     for (int l = 0; l < D; ++l) {
         x[l] = nu_icdf<R>(P, n[l]);
-        if (want_phase) ph[l] = u_phase<R>(n[l]);
+        if (want_phase) ph[l] = u_phase<R>(n[l], P.half_angle != 0);
     }
 }
 
@@ -275,7 +283,7 @@ __device__ __forceinline__ void start_phases_dev(const QrParams& P, int i, long 
     uint64_t n[D];
     start_ints<D>(P, i, (uint32_t)m, n);
 #pragma unroll
-    for (int l = 0; l < D; ++l) ph[l] = u_phase<R>(n[l]);
+    for (int l = 0; l < D; ++l) ph[l] = u_phase<R>(n[l], P.half_angle != 0);
 }
 
 // Euler step of Sec. 2.1.1 with constant b and sigma

@@ -10,7 +10,6 @@ namespace qr {
 
 constexpr int kDMax = 8;    // dimensions
 constexpr int kNMax = 256;  // time steps
-constexpr int kKMax = 7;    // max |k_l| (int8 table, small power tables)
 
 enum { QR_TAG_START = 0, QR_TAG_INCR = 1, QR_TAG_TEST = 2 };
 
@@ -19,7 +18,7 @@ enum : unsigned { ST_TIMEOUT = 1u };
 
 // counters[0] = clamp hits, counters[1] = non-finite responses,
 // counters[2] = residual (bits of a non-negative double, atomicMax)
-enum { CNT_CLAMP = 0, CNT_NONFINITE = 1, CNT_RESID = 2, CNT_N = 4 };
+enum { CNT_CLAMP = 0, CNT_NONFINITE = 1, CNT_RESID = 2, CNT_SPARE = 3, CNT_N = 4 };
 
 // One entry of the coefficient table: k (int8 per dimension). The table is
 // [k = 0, then Gamma_+ = {k : first nonzero k_l > 0}] in canonical order;
@@ -49,6 +48,7 @@ struct QrParams {
     int lattice_n;
     int chunk;     // projection: paths per CTA
     int n_chunks;  // ceil(M / chunk)
+    int half_angle;  // cosine basis: phases e^{i pi F(x)} instead of e^{2 pi i F(x)}
 };
 
 // kernel launchers (qr_kernels.cu); all asynchronous on `st`
@@ -62,6 +62,10 @@ cudaError_t launch_reduce(int prec, const QrParams& P, const double2* partial, d
                           unsigned long long* counters, cudaStream_t st);
 cudaError_t launch_pack(int prec, const QrParams& P, const double2* alpha, int nG, int zero_idx,
                         void* packed, long long row_stride, int rows, cudaStream_t st);
+// cosine basis: symmetrise the raw projections of rows [i_lo, i_hi) over the
+// sign orbits (CSR orb_off/orb_idx over the canonical Z^d order) into alpha
+cudaError_t launch_sym_cos(const double2* raw, double2* alpha, int nG, const int* orb_off, const int* orb_idx,
+                           int i_lo, int i_hi, unsigned long long* counters, cudaStream_t st);
 cudaError_t launch_eval(int prec, const QrParams& P, const GEntry* tab, const uint8_t* first,
                         const void* packed_row, const double* x, long long n, double* y, int use_g,
                         cudaStream_t st);

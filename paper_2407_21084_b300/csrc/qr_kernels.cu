@@ -246,7 +246,7 @@ __device__ __forceinline__ void start_phases(const QrParams& P, int i, long long
     uint64_t n[D];
     start_ints<D>(P, i, (uint32_t)m, n);
 #pragma unroll
-    for (int l = 0; l < D; ++l) ph[l] = u_phase<R>(n[l]);
+    for (int l = 0; l < D; ++l) ph[l] = u_phase<R>(n[l], P.half_angle != 0);
 }
 
 template <typename R, int D, int BS>
@@ -346,6 +346,45 @@ __global__ void k_reduce(const __grid_constant__ QrParams P, const double2* __re
         packed[(size_t)i * row_stride + e] = e == 0 ? mk2<R>((R)sx, (R)0) : mk2<R>((R)(2.0 * sx), (R)(2.0 * sy));
     }
     // block max, then one atomic (max is order independent)
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) diff = fmax(diff, __shfl_xor_sync(0xffffffffu, diff, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = diff;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+        atomicMax(&counters[CNT_RESID], (unsigned long long)__double_as_longlong(mx));
+    }
+}
+
+// Cosine basis (Lemma ortho:dim1) through the unfolded Fourier set: with
+// v = F(x)/2, C_k(F(x)) = prod_l w_l cos(2 pi k_l v_l) expands over the sign
+// orbit of k, so a cosine series is the Z^d series with the real, sign-
+// symmetric coefficients c_m = a_|m| prod_{m_l != 0} (w/2), evaluated at the
+// half-angle phases, and the Monte-Carlo cosine projection of eq. (Aqi:bar:M)
+// is, in the same coordinates, the average of Re alpha over the sign orbit:
+//     c_m = 2^-d'(m) sum_{s in orbit(m)} Re alpha_s.
+// Reads the raw projections of rows [i_lo, i_hi), writes c into alpha and the
+// residual max(|c - c_old|) into counters[CNT_RESID].
+__global__ void k_sym_cos(const double2* __restrict__ raw, double2* __restrict__ alpha, int nG,
+                          const int* __restrict__ orb_off, const int* __restrict__ orb_idx, int i_lo, int i_hi,
+                          unsigned long long* __restrict__ counters)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)(i_hi - i_lo) * nG;
+    double diff = 0.0;
+    if (idx < total) {
+        const int i = i_lo + (int)(idx / nG), e = (int)(idx % nG);
+        const double2* r = raw + (size_t)i * nG;
+        const int a = orb_off[e], b = orb_off[e + 1];
+        double s = 0.0;
+        for (int t = a; t < b; ++t) s += r[orb_idx[t]].x;
+        s /= (double)(b - a);
+        double2* row = alpha + (size_t)i * nG;
+        const double2 old = row[e];
+        diff = hypot(s - old.x, old.y);
+        row[e] = make_double2(s, 0.0);
+    }
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) diff = fmax(diff, __shfl_xor_sync(0xffffffffu, diff, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = diff;
@@ -641,6 +680,16 @@ cudaError_t launch_sample(int prec, const QrParams& P, int i, long long m0, long
         QR_DISPATCH_D(sample_t, float, P, i, m0, n, j, u, x, z, st)
     }
     QR_DISPATCH_D(sample_t, double, P, i, m0, n, j, u, x, z, st)
+}
+
+cudaError_t launch_sym_cos(const double2* raw, double2* alpha, int nG, const int* orb_off, const int* orb_idx,
+                           int i_lo, int i_hi, unsigned long long* counters, cudaStream_t st)
+{
+    const long long total = (long long)(i_hi - i_lo) * nG;
+    if (total <= 0) return cudaSuccess;
+    k_sym_cos<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(raw, alpha, nG, orb_off, orb_idx, i_lo, i_hi,
+                                                               counters);
+    return cudaGetLastError();
 }
 
 }  // namespace qr

@@ -73,6 +73,10 @@ extern "C" qr_status qr_project_static(qr_ctx* ctx, const void* S, int i_lo, int
         return QR_EINVAL;
     }
     const qr::QrParams& P = *v.P;
+    if (P.half_angle) {
+        qr::ctx_set_error(ctx, "qr_project_static: the cosine basis is not supported");
+        return QR_ENOTIMPL;
+    }
     const size_t need = (size_t)(i_hi - i_lo) * (size_t)P.n_chunks * (size_t)P.nGp;
     if (need > kPartialSlots) {
         char msg[200];

@@ -10,7 +10,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib as L
-from .workloads import Workload
+from .workloads import Sec5Problem, Workload
 
 
 def _dp(a: np.ndarray):
@@ -27,6 +27,8 @@ class Solver:
         self.precision = precision
         b = np.ascontiguousarray(b, dtype=np.float64)
         sigma = np.ascontiguousarray(sigma, dtype=np.float64).reshape(-1)
+        if b.size != d or sigma.size != d * d:
+            raise ValueError("b needs d and sigma d*d entries (d = %d)" % d)
         fp = np.ascontiguousarray(np.atleast_1d(f_par), dtype=np.float64)
         gp = np.ascontiguousarray(np.atleast_1d(g_par), dtype=np.float64)
         self._keep = (b, sigma, fp, gp)
@@ -64,6 +66,24 @@ class Solver:
         return cls(w.d, w.N, w.T, w.nu_kind, w.mu, w.gamma_kind, w.gamma_n, w.b, w.sigma, L.QR_F_CUBIC_MANUF,
                    w.f_par, L.QR_GT_COS, w.g_par, w.M if M is None else M, w.seed, precision=precision,
                    clamp_L=w.clamp_L if clamp else 0.0, stream=stream, path_kernel=path_kernel, instance=instance)
+
+    @classmethod
+    def from_sec5(cls, p: Sec5Problem, precision=L.QR_FP64, M=None, stream=None, instance=0, path_kernel=0):
+        """The test problem of Sec. 5 (Student nu, min/sin driver and terminal
+        condition, cosine basis), no truncation."""
+        return cls(p.d, p.N, p.T, L.QR_NU_STUDENT2, 2.0, p.gamma_kind, p.gamma_n, p.b, p.sigma,
+                   L.QR_F_PAPER_MIN, p.f_par, L.QR_GT_PAPER_SIN, p.g_par, p.M if M is None else M, p.seed,
+                   precision=precision, clamp_L=0.0, stream=stream, instance=instance, path_kernel=path_kernel)
+
+    def cosine_coefs(self):
+        """For a context of the cosine basis (N^d set): the N^d multi-indices
+        (canonical order) and the cosine coefficients a_k of every row,
+        a_k = 2^{d'(k)/2} c_k from the unfolded coefficients c_m."""
+        k = self.gamma_list()
+        keep = np.all(k >= 0, axis=1)
+        c = self.coefs()[:, keep].real
+        dnz = np.count_nonzero(k[keep], axis=1)
+        return k[keep], c * np.sqrt(2.0) ** dnz
 
     # -------------------------------------------------------------- calls
     def picard_step(self, n_iter: int = 1) -> float:

@@ -46,7 +46,10 @@ class Workload:
     def __post_init__(self):
         if self.b is None:
             self.b = np.zeros(self.d)
+        self.b = np.asarray(self.b, dtype=np.float64)
         self.s = np.asarray(self.s, dtype=np.float64)
+        if self.b.shape != (self.d,) or self.s.shape != (self.d,):
+            raise ValueError("b and s must have d = %d entries" % self.d)
 
     @property
     def sigma(self) -> np.ndarray:
@@ -77,6 +80,8 @@ class Workload:
 
     def with_(self, **kw) -> "Workload":
         d = dict(self.__dict__)
+        if "d" in kw and "b" not in kw:
+            d["b"] = None  # the drift follows the dimension (zero)
         d.update(kw)
         return Workload(**d)
 
@@ -139,6 +144,53 @@ def c4(n_instances: int = 256, n_shared: int = 64, M: int = 2 ** 18, seed: int =
                                 M=M, n_iter=1, a=float(rng.uniform(0.0, 0.5)), s=rng.uniform(-1.0, 1.0, size=d),
                                 seed=4999))
     return out
+
+
+@dataclass
+class Sec5Problem:
+    """The test problem of Sec. 5 of the paper: dX = dW (sigma = I, b = 0),
+    g = 1 + kappa + sin(lam sum x), f = min(1, [y - kappa - 1 - sin(lam sum x)
+    e^{lam^2 d (t-T)/2}]^2), exact solution u = 1 + kappa + sin(lam sum x)
+    e^{lam^2 d (t-T)/2}; kappa = 0.6, lam = 1/sqrt(d), T = 1; Student nu with
+    mu = 2; cosine basis on an N^d set (Gamma_F, Gamma_T or Gamma_H)."""
+
+    d: int
+    N: int
+    gamma_kind: int
+    gamma_n: int
+    M: int
+    seed: int
+    T: float = 1.0
+    kappa: float = 0.6
+
+    @property
+    def lam(self) -> float:
+        return 1.0 / np.sqrt(self.d)
+
+    @property
+    def sigma(self) -> np.ndarray:
+        return np.eye(self.d)
+
+    @property
+    def b(self) -> np.ndarray:
+        return np.zeros(self.d)
+
+    @property
+    def f_par(self) -> np.ndarray:
+        return np.array([self.kappa, self.lam])
+
+    @property
+    def g_par(self) -> np.ndarray:
+        return np.array([self.kappa, self.lam])
+
+    def exact_u(self, t: float, x: np.ndarray) -> np.ndarray:
+        sx = np.atleast_2d(x).sum(axis=1)
+        return 1.0 + self.kappa + np.sin(self.lam * sx) * np.exp(self.lam ** 2 * self.d * (t - self.T) / 2.0)
+
+
+def sec5_d1(K: int, N: int, M: int, seed: int) -> Sec5Problem:
+    """d = 1 rows of the paper's Sec. 5 (Delta = 1/N, K + 1 cosines, M paths)."""
+    return Sec5Problem(d=1, N=N, gamma_kind=G_FULL_N, gamma_n=K, M=M, seed=seed)
 
 
 CONFIGS = {"c1": c1, "c2": c2, "c3": c3}

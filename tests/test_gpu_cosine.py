@@ -1,0 +1,107 @@
+"""GPU parity of the cosine basis (Sec. 2.2, Lemma ortho:dim1) on the N^d
+sets Gamma_F, Gamma_T, Gamma_H against the FP64 oracle, which evaluates the
+cosines directly (the CUDA path runs the unfolded Z^d set at half angles and
+averages the projections over sign orbits). Also the paper's d = 1 test
+problem of Sec. 5: 50 independent runs give a 99 % interval for u(0,0) that
+contains 1.6 and overlaps the paper's [1.578, 1.667]."""
+import numpy as np
+import pytest
+
+from paper_2407_21084_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_21084_b300 import build, solver
+
+    build.build()
+    return solver
+
+
+def _oracle_problem(ora, p: W.Sec5Problem, M=None):
+    K = ora.gamma_list(p.gamma_kind, p.d, p.gamma_n)
+    return ora.Problem(d=p.d, N=p.N, T=p.T, k=K, b=p.b, sigma=p.sigma, f_kind=ora.F_PAPER_MIN, f_par=p.f_par,
+                       g_kind=ora.GT_PAPER_SIN, g_par=p.g_par, M=p.M if M is None else M, seed=p.seed,
+                       nu_kind=ora.NU_STUDENT2, mu=2.0, basis=ora.BASIS_COS)
+
+
+@pytest.mark.parametrize("d,kind,n,N,M", [
+    (1, W.G_FULL_N, 100, 6, 3000),   # generic table kernel, 101 cosines
+    (2, W.G_TOTAL_N, 6, 5, 2500),
+    (2, W.G_HYP_N, 7, 5, 2500),
+    (3, W.G_TOTAL_N, 3, 4, 1500),
+    (6, W.G_TOTAL_N, 5, 4, 1100),    # unfolds to |k|_1 <= 5: compile-time tree kernels
+])
+def test_cosine_picard_matches_oracle(mods, ora, d, kind, n, N, M):
+    solver = mods
+    p = W.Sec5Problem(d=d, N=N, gamma_kind=kind, gamma_n=n, M=M, seed=9)
+    ref, _ = ora.picard(_oracle_problem(ora, p), 2)
+    ref = ref.real
+    for prec, tol in ((0, 1e-10), (1, 1e-4)):
+        with solver.Solver.from_sec5(p, precision=prec) as s:
+            s.picard_step(2)
+            k, a = s.cosine_coefs()
+        assert np.array_equal(k, ora.gamma_list(kind, d, n))
+        err = np.abs(a - ref).max() / np.abs(ref).max()
+        assert err < tol, (prec, err)
+
+
+def test_cosine_backward_sweep_matches_oracle(mods, ora):
+    solver = mods
+    p = W.sec5_d1(K=100, N=20, M=20000, seed=3)
+    ref, _ = ora.backward_sweep(_oracle_problem(ora, p))
+    with solver.Solver.from_sec5(p, precision=0) as s:
+        s.backward_sweep()
+        _, a = s.cosine_coefs()
+        y0 = float(s.eval(0, np.zeros((1, 1)))[0])
+    assert np.abs(a - ref.real).max() / np.abs(ref.real).max() < 1e-10
+    y0_ref = float(np.atleast_1d(ora.series(_oracle_problem(ora, p), ref[0], np.zeros((1, 1))))[0])
+    assert abs(y0 - y0_ref) < 1e-10
+
+
+def test_cosine_planted_polynomial_on_lattice(mods, ora):
+    """sigma = 0, f = 0, g = a cosine polynomial given through its unfolded
+    coefficients: every row recovers it exactly on the midpoint lattice."""
+    solver = mods
+    from paper_2407_21084_b300 import _lib as L
+
+    d, n, lat = 2, 4, 5
+    rng = np.random.default_rng(4)
+    Kn = ora.gamma_list(W.G_TOTAL_N, d, n)
+    a = rng.normal(size=len(Kn))
+    Kz = ora.gamma_list(W.G_L1_Z, d, n)
+    where = {tuple(k): e for e, k in enumerate(Kn)}
+    cz = np.array([a[where[tuple(np.abs(m))]] * 2.0 ** (-np.count_nonzero(m) / 2) for m in Kz])
+    g = np.zeros((len(Kz), 2))
+    g[:, 0] = cz
+    for prec, tol in ((0, 1e-12), (1, 1e-5)):
+        with solver.Solver(d, 3, 1.0, L.QR_NU_STUDENT2, 2.0, L.QR_G_TOTAL_N, n, np.zeros(d), np.zeros((d, d)),
+                           L.QR_F_ZERO, [0.0], L.QR_GT_TRIGPOLY, g.ravel(), lat ** d, 1, precision=prec,
+                           lattice_n=lat) as s:
+            s.picard_step(1)
+            k, got = s.cosine_coefs()
+        assert np.array_equal(k, Kn)
+        assert np.abs(got - a[None, :]).max() < tol * np.abs(a).max()
+
+
+def test_paper_d1_confidence_interval(mods):
+    """Sec. 5, d = 1, Delta = 0.05, K = 100, M = 2 10^4, q = 0: the paper's
+    99 % interval for ybar_0(0) over 50 runs is [1.578, 1.667], u(0,0) = 1.6."""
+    solver = mods
+    vals = []
+    for seed in range(1, 51):
+        p = W.sec5_d1(K=100, N=20, M=20000, seed=seed)
+        with solver.Solver.from_sec5(p, precision=1) as s:
+            s.backward_sweep()
+            vals.append(float(s.eval(0, np.zeros((1, 1)))[0]))
+    v = np.array(vals)
+    half = 2.576 * v.std(ddof=1) / np.sqrt(len(v))
+    lo, hi = v.mean() - half, v.mean() + half
+    assert lo <= 1.6 <= hi, (lo, hi)
+    assert lo <= 1.667 and hi >= 1.578, (lo, hi)
