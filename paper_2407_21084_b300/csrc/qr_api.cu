@@ -460,7 +460,8 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     for (int l = 0; l < d; ++l)
         if (c->k[(size_t)c->zero_idx * d + l] != 0) return bail(QR_EINVAL, "index set is not symmetric");
     for (int v : c->k) c->kmax = std::max(c->kmax, v < 0 ? -v : v);
-    if (c->kmax > 127) return bail(QR_ENOTIMPL, "|k_l| <= 127 is required");
+    if (c->kmax > gentry_kmax(d))
+        return bail(QR_ENOTIMPL, d <= 4 ? "|k_l| <= 32767 is required" : "|k_l| <= 127 is required for d > 4");
     {
         // the table kernels (generic path, projection, evaluation) keep the
         // powers z_l^a, a <= max|k_l|, of every lane in shared memory
@@ -475,11 +476,11 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     std::vector<GEntry> tab(c->nGp);
     std::vector<uint8_t> first(c->nGp, 0);
     for (int e = 0; e < c->nGp; ++e) {
-        std::memset(tab[e].k, 0, sizeof(tab[e].k));
-        for (int l = 0; l < d && l < kDMax; ++l) tab[e].k[l] = (signed char)c->k[(size_t)(c->zero_idx + e) * d + l];
+        std::memset(tab[e].k8, 0, sizeof(tab[e].k8));
+        for (int l = 0; l < d && l < kDMax; ++l) tab[e].set(d, l, c->k[(size_t)(c->zero_idx + e) * d + l]);
         if (e > 0) {
             int f0 = 0;
-            while (f0 < d && tab[e].k[f0] == tab[e - 1].k[f0]) ++f0;
+            while (f0 < d && tab[e].get(d, f0) == tab[e - 1].get(d, f0)) ++f0;
             first[e] = (uint8_t)f0;
         }
     }

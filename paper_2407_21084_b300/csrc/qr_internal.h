@@ -20,12 +20,31 @@ enum : unsigned { ST_TIMEOUT = 1u };
 // counters[2] = residual (bits of a non-negative double, atomicMax)
 enum { CNT_CLAMP = 0, CNT_NONFINITE = 1, CNT_RESID = 2, CNT_SPARE = 3, CNT_N = 4 };
 
-// One entry of the coefficient table: k (int8 per dimension). The table is
-// [k = 0, then Gamma_+ = {k : first nonzero k_l > 0}] in canonical order;
-// first[e] is the first dimension in which entry e differs from entry e-1.
+// One entry of the coefficient table: k, as int16 per dimension for d <= 4
+// (|k_l| <= 32767: the long one-dimensional sets of Sec. 5) or int8 for
+// d > 4 (|k_l| <= 127). The table is [k = 0, then Gamma_+ = {k : first
+// nonzero k_l > 0}] in canonical order; first[e] is the first dimension in
+// which entry e differs from entry e-1.
 struct alignas(8) GEntry {
-    signed char k[8];
+    union {
+        signed char k8[8];
+        short k16[4];
+    };
+    template <int D>
+    __host__ __device__ __forceinline__ int kv(int l) const
+    {
+        return D <= 4 ? (int)k16[l] : (int)k8[l];
+    }
+    __host__ int get(int d, int l) const { return d <= 4 ? (int)k16[l] : (int)k8[l]; }
+    __host__ void set(int d, int l, int v)
+    {
+        if (d <= 4)
+            k16[l] = (short)v;
+        else
+            k8[l] = (signed char)v;
+    }
 };
+constexpr int gentry_kmax(int d) { return d <= 4 ? 32767 : 127; }
 
 struct QrParams {
     int d, N, nGp, K1;  // K1 = max|k_l| + 1

@@ -52,7 +52,7 @@ __device__ __forceinline__ void basis_step(V2<R> (&b)[D], const GEntry& g, int f
 #pragma unroll
     for (int l = 0; l < D; ++l) {
         if (l >= f) {
-            const int v = g.k[l];
+            const int v = g.template kv<D>(l);
             V2<R> prev = (l == 0) ? mk2<R>((R)1, (R)0) : b[l - 1];
             if (v == 0) {
                 b[l] = prev;

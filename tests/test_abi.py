@@ -64,7 +64,8 @@ def _init(lib, d=2, N=4, T=1.0, gamma=(1, 2), M=64, prec=0, fkind=0, gkind=0, nu
 @pytest.mark.parametrize("kw,frag", [
     (dict(d=0), "d must"), (dict(d=9), "d must"), (dict(N=0), "N must"), (dict(N=257), "N must"),
     (dict(T=-1.0), "T must"), (dict(M=0), "M must"), (dict(prec=7), "precision"),
-    (dict(gamma=(6, 2)), "index set"), (dict(gamma=(5, 0)), "index set"), (dict(d=1, gamma=(0, 128)), "|k_l| <= 127"),
+    (dict(gamma=(6, 2)), "index set"), (dict(gamma=(5, 0)), "index set"), (dict(d=5, gamma=(2, 128)), "|k_l| <= 127"),
+    (dict(d=1, gamma=(0, 40000)), "|k_l| <= 32767"),
     (dict(d=1, gamma=(3, 120)), "too large for the table kernels"), (dict(nu=(0, -1.0)), "mu"),
     (dict(fkind=9), "driver"), (dict(gkind=9), "terminal"), (dict(lattice=3, M=10), "lattice"),
 ])
