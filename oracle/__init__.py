@@ -66,6 +66,7 @@ class _Problem(C.Structure):
         ("clamp_L", C.c_double),
         ("lattice_n", C.c_int),
         ("basis", C.c_int),
+        ("q_damp", C.c_double),
     ]
 
 
@@ -199,6 +200,7 @@ class Problem:
     clamp_L: float = 0.0
     lattice_n: int = 0
     basis: int = 0  # BASIS_FOURIER (k in Z^d) or BASIS_COS (k in N^d, real coefficients)
+    q_damp: float = 0.0  # damping exponent q of eq. (yqi)
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> _Problem:
@@ -214,7 +216,7 @@ class Problem:
             self.d, self.N, self.T, self.nu_kind, self.mu, k.shape[0],
             k.ctypes.data_as(C.POINTER(C.c_int)), int(np.abs(k).max()) if k.size else 0,
             _dp(b), _dp(s), self.f_kind, _dp(fp), self.g_kind, _dp(gp), self.M,
-            self.seed, self.instance, self.clamp_L, self.lattice_n, self.basis,
+            self.seed, self.instance, self.clamp_L, self.lattice_n, self.basis, self.q_damp,
         )
 
     @property

@@ -16,7 +16,8 @@
  *                           C_0 = 1, C_k = sqrt(2) cos(k pi u), k in N, of
  *                           Lemma (ortho:dim1) itself; Lemma (eqInnerNorms)
  *                           makes phi_k orthonormal in L2_nu in both cases.
- *   response S_i            Sec. 2.3, Algorithm 1, eq. (Sqi:bar:M) with q = 0
+ *   response S_i            Sec. 2.3, Algorithm 1, eq. (Sqi:bar:M), damping
+ *                           exponent q of eq. (yqi) (q = 0: no weight)
  *   truncation T_L          Sec. 1 notation, eq. (TL:2), constant L
  *   coefficients            Sec. 2.3, Algorithm 1, eq. (Aqi:bar:M): plain
  *                           Monte-Carlo average, no linear solve
@@ -352,6 +353,14 @@ static void start_point(const ora_problem* p, int i, long long m, double* u)
     }
 }
 
+/* Damping weight (1 + |x|^2)^{q/2} of eq. (yqi). */
+static double damp_weight(const ora_problem* p, const double* x)
+{
+    double r2 = 0;
+    for (int l = 0; l < p->d; ++l) r2 += x[l] * x[l];
+    return pow(1.0 + r2, 0.5 * p->q_damp);
+}
+
 double ora_response(const ora_problem* p, const double* alpha, int i, long long m, double* u_out,
                     long long* clamp_hits)
 {
@@ -360,6 +369,7 @@ double ora_response(const ora_problem* p, const double* alpha, int i, long long 
     double x[32], x1[32], z[32];
     start_point(p, i, m, u_out);
     for (int l = 0; l < d; ++l) x[l] = ora_nu_icdf(p->nu_kind, p->mu, u_out[l]); /* X_i^i ~ nu */
+    double w_start = p->q_damp != 0.0 ? damp_weight(p, x) : 1.0;
     double sum_f = 0.0;
     for (int j = i; j < N; ++j) {
         /* Euler step: X_{j+1} = X_j + b dt + sigma (W_{t_{j+1}} - W_{t_j}) */
@@ -375,7 +385,10 @@ double ora_response(const ora_problem* p, const double* alpha, int i, long long 
         if (j + 1 == N) {
             y1 = ora_g(p, x1);
         } else {
+            /* the series represents the damped ybar^q_{j+1} (eq. yqi:bar:M):
+             * y_{j+1} = ybar^q_{j+1}(X_{j+1}) (1 + |X_{j+1}|^2)^{q/2} */
             y1 = ora_series(p, alpha + (size_t)2 * (size_t)(j + 1) * (size_t)p->nG, x1);
+            if (p->q_damp != 0.0) y1 *= damp_weight(p, x1);
             if (p->clamp_L > 0) {
                 if (y1 > p->clamp_L) {
                     y1 = p->clamp_L;
@@ -389,7 +402,9 @@ double ora_response(const ora_problem* p, const double* alpha, int i, long long 
         sum_f += ora_f(p, (double)j * dt, x, y1) * dt; /* f_j(X_j, y_{j+1}) dt */
         memcpy(x, x1, sizeof(double) * (size_t)d);
     }
-    return ora_g(p, x) + sum_f; /* S_i = g(X_N) + sum_j f_j(...) dt */
+    /* S^q_i = [g(X_N) + sum_j f_j(...) dt] / (1 + |X_i^i|^2)^{q/2}, eq. (Sqi:bar:M) */
+    double S = ora_g(p, x) + sum_f;
+    return p->q_damp != 0.0 ? S / w_start : S;
 }
 
 static long long chunk_len(long long len)

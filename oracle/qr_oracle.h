@@ -22,6 +22,11 @@
  *                        on a midpoint lattice; sampled orthonormality; the
  *                        paper's d = 1 confidence intervals for u(0,0) = 1.6
  *                        (Sec. 5) on its own test PDE.
+ *   damping q            pinned: with sigma = 0 on a lattice the damped
+ *                        linear-driver iterate is (1 + lambda dt)^{N-i} times
+ *                        the lattice projection of g / w; Feynman-Kac with
+ *                        f = 0 against the exact damped coefficients by
+ *                        1-D quadrature.
  *   ora_picard_iter      pinned: planted trigonometric polynomial recovered
  *                        exactly on a lattice; the linear driver closed form;
  *                        Feynman-Kac (f=0, drift) against exact coefficients
@@ -122,6 +127,8 @@ typedef struct {
     double clamp_L;      /* <= 0: no truncation */
     int lattice_n;       /* > 0: start points on the centred lattice (n^d = M) instead of Philox */
     int basis;           /* ORA_BASIS_FOURIER (k in Z^d) or ORA_BASIS_COS (k in N^d, real alpha) */
+    double q_damp;       /* damping exponent q of eq. (yqi): the series represents
+                          * ybar^q = y / (1 + |x|^2)^{q/2}; 0 = undamped */
 } ora_problem;
 
 /* Series y(x) = Re sum_{k in Gamma} alpha_k phi_k(x), phi_k(x) = prod_l e^{2 pi i k_l F(x_l)}
