@@ -99,6 +99,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, ws: int) -> float:
+    """Job time of a replica run: the slowest rank's time (all-reduce MAX;
+    on the GPU tensor for NCCL, on a CPU tensor for gloo)."""
+    if ws == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(evals_per_step: float, ms_step: float, ws: int) -> float:
+    """Whole-job throughput of ws replicas, each doing evals_per_step per step."""
+    return ws * evals_per_step / (ms_step / 1e3)
+
+
 def cpu_baseline(w: W.Workload, alpha_prev: np.ndarray, rows, m_sample: int, gpu_rows: dict | None):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample:
     rows `rows` of one Picard iteration from alpha_prev over the first
@@ -224,15 +243,12 @@ def main():
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
-    total_ms = float(np.sum(step_ms))
+    total_ms = max_over_ranks(float(np.sum(step_ms)), ws)
     if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     evals = w.evals_per_iter()
     ms_step = total_ms / args.steps
-    value = ws * evals / (ms_step / 1e3)
+    value = job_value(evals, ms_step, ws)
 
     # dominant kernel: the path-and-series kernel, timed by the library's
     # events on its launch stream over the timed region
@@ -268,7 +284,7 @@ def main():
         s.picard_step(1)
         a_host = s.coefs()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_val = ws * evals / (np.mean(e2e_ms) / 1e3)
+    e2e_val = job_value(evals, max_over_ranks(float(np.mean(e2e_ms)), ws), ws)
     io_bytes = w.N * nG * 16
 
     line = {

@@ -142,6 +142,12 @@ typedef struct {
     int path_kernel;          /* 0: the compile-time tree kernel when one is built for this
                                  index set (|k|_1 or |k|_inf sets of the benchmark workloads),
                                  else the table-driven kernel; 1: always the table-driven kernel */
+    double damping_q;         /* damping exponent q >= 0 of eq. (yqi), 0 = none: the
+                                 coefficients represent ybar^q = y / (1 + |x|^2)^{q/2};
+                                 responses follow eq. (Sqi:bar:M) (the series at X_{j+1}
+                                 is multiplied by the weight before T_L and f, the
+                                 response divided by the weight at X_i^i); qr_eval
+                                 returns ybar^q. A QR_GT_TRIGPOLY g stays undamped. */
 } qr_opts;
 
 /* Creates a context: validates the problem, enumerates Gamma, allocates the

@@ -56,6 +56,7 @@ class QrOpts(C.Structure):
         ("lattice_n", C.c_int),
         ("instance", C.c_int),
         ("path_kernel", C.c_int),
+        ("damping_q", C.c_double),
     ]
 
 

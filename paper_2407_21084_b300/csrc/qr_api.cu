@@ -440,6 +440,7 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     if (o.M < 1 || o.M > (1ll << 32)) return bail(QR_EINVAL, "M must be in [1, 2^32]");
     if (o.precision != QR_FP32 && o.precision != QR_FP64) return bail(QR_EINVAL, "unknown precision");
     if (o.instance < 0 || o.instance >= 4096) return bail(QR_EINVAL, "instance must be in [0, 4096)");
+    if (!(o.damping_q >= 0.0) || !std::isfinite(o.damping_q)) return bail(QR_EINVAL, "damping_q must be >= 0");
     if (o.uniform_source == QR_U_LATTICE) {
         if (o.lattice_n < 1) return bail(QR_EINVAL, "lattice_n must be positive");
         long long L = 1;
@@ -489,6 +490,7 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     QrParams& P = c->P;
     P.d = d;
     P.half_angle = cosine ? 1 : 0;
+    P.q_damp = o.damping_q;
     P.N = N;
     P.nGp = c->nGp;
     P.K1 = c->kmax + 1;
@@ -1045,11 +1047,12 @@ qr_status batch_build_groups(qr_batch* b)
         if (seen[q]) continue;
         const qr_ctx* c = b->ctx[q];
         if (!group_supported(c->gkind, c->d, c->gn) || !c->d_perm || c->N > kGroupNMax) continue;
-        if (c->P.f_kind != QR_F_CUBIC_MANUF || c->P.g_kind != QR_GT_COS) continue;
+        if (c->P.f_kind != QR_F_CUBIC_MANUF || c->P.g_kind != QR_GT_COS || c->P.q_damp != 0.0) continue;
         std::vector<int> mem;
         for (int r = q; r < n; ++r) {
             const qr_ctx* e = b->ctx[r];
-            if (!seen[r] && e->P.f_kind == QR_F_CUBIC_MANUF && e->P.g_kind == QR_GT_COS && shares_points(c, e))
+            if (!seen[r] && e->P.f_kind == QR_F_CUBIC_MANUF && e->P.g_kind == QR_GT_COS && e->P.q_damp == 0.0 &&
+                shares_points(c, e))
                 mem.push_back(r);
         }
         if ((int)mem.size() < b->group_min) continue;

@@ -286,6 +286,28 @@ __device__ __forceinline__ void start_phases_dev(const QrParams& P, int i, long 
     for (int l = 0; l < D; ++l) ph[l] = u_phase<R>(n[l], P.half_angle != 0);
 }
 
+// Damping of eq. (yqi): the series represents ybar^q = y / w(x),
+// w(x) = (1 + |x|^2)^{q/2}. log w with qh = q/2:
+template <typename R, int D>
+__device__ __forceinline__ R damp_logw(R qh, const R (&x)[D])
+{
+    R r2 = 0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) r2 += x[l] * x[l];
+    return qh * ((sizeof(R) == 4) ? (R)log1pf((float)r2) : (R)log1p((double)r2));
+}
+
+// y w(x) from y and log w, formed in the log domain so that a weight that
+// alone would overflow does not (y = 0 stays 0)
+template <typename R>
+__device__ __forceinline__ R undamp(R y, R lw)
+{
+    const R a = y < (R)0 ? -y : y;
+    if (a == (R)0) return y;
+    const R v = (sizeof(R) == 4) ? (R)expf((float)(lw + (R)logf((float)a))) : (R)exp((double)lw + log((double)a));
+    return y < (R)0 ? -v : v;
+}
+
 // Euler step of Sec. 2.1.1 with constant b and sigma
 template <typename R, int D>
 __device__ __forceinline__ void euler(const QrParams& P, const R (&x)[D], const R (&z)[D], R (&x1)[D])

@@ -68,6 +68,7 @@ struct QrParams {
     int chunk;     // projection: paths per CTA
     int n_chunks;  // ceil(M / chunk)
     int half_angle;  // cosine basis: phases e^{i pi F(x)} instead of e^{2 pi i F(x)}
+    double q_damp;   // damping exponent q of eq. (yqi); 0: none
 };
 
 // kernel launchers (qr_kernels.cu); all asynchronous on `st`

@@ -155,6 +155,9 @@ __global__ void __launch_bounds__(BS) k_paths(const __grid_constant__ QrParams P
         V2<R> unused[D];
         start_point<R, D>(P, i, m, x, unused, false);
     }
+    const bool damp = P.q_damp != 0.0;
+    const R qh = (R)(0.5 * P.q_damp);
+    const R lw0 = damp ? damp_logw<R, D>(qh, x) : (R)0;  // log w(X_i^i)
     R sum = 0, comp = 0, gN = 0;
     unsigned long long hits = 0;
     V2<R>* mypw = pw + tid;
@@ -194,6 +197,7 @@ __global__ void __launch_bounds__(BS) k_paths(const __grid_constant__ QrParams P
             for (int l = 0; l < D; ++l) zz[l] = nu_phase<R>(P, x1[l]);
             fill_powers<R, D>(mypw, K1, BS, zz);
             y = series<R, D>(abuf[buf], tab, first, nGp, mypw, K1, BS);
+            if (damp && row < N) y = undamp<R>(y, damp_logw<R, D>(qh, x1));  // y = ybar^q w(X_{j+1})
             if (row < N && P.clamp_L > 0.0) {
                 const R L = (R)P.clamp_L;
                 if (y > L) {
@@ -218,7 +222,8 @@ __global__ void __launch_bounds__(BS) k_paths(const __grid_constant__ QrParams P
         for (int l = 0; l < D; ++l) x[l] = x1[l];
         __syncthreads();
     }
-    const R Sv = gN + sum;
+    // S^q_i = [g(X_N) + sum_j f dt] / w(X_i^i), eq. (Sqi:bar:M)
+    const R Sv = damp ? (gN + sum) * (R)exp((double)-lw0) : gN + sum;
     unsigned long long bad = 0;
     if (active) {
         S[(size_t)(i - i_lo) * (size_t)P.M + (size_t)m] = Sv;
@@ -512,12 +517,11 @@ static size_t paths_smem(const QrParams& P, long long row_stride, int D, int BS)
            (size_t)D * P.K1 * BS * sizeof(V2<R>) + 16;
 }
 
-template <typename R, int D>
-static cudaError_t paths_t(const QrParams& P, const GEntry* tab, const uint8_t* first, const void* packed,
-                           long long row_stride, void* S, int i_lo, int i_hi, unsigned long long* counters,
-                           unsigned* status, cudaStream_t st)
+template <typename R, int D, int BS>
+static cudaError_t paths_bs(const QrParams& P, const GEntry* tab, const uint8_t* first, const void* packed,
+                            long long row_stride, void* S, int i_lo, int i_hi, unsigned long long* counters,
+                            unsigned* status, cudaStream_t st)
 {
-    constexpr int BS = sizeof(R) == 4 ? kBS32 : kBS64;
     const size_t sm = paths_smem<R>(P, row_stride, D, BS);
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
     auto kern = k_paths<R, D, BS>;
@@ -531,11 +535,22 @@ static cudaError_t paths_t(const QrParams& P, const GEntry* tab, const uint8_t* 
     return cudaGetLastError();
 }
 
+// FP32 runs 256-thread blocks when their power tables fit in shared memory,
+// else 128 (long one-dimensional sets); FP64 always 128
 template <typename R, int D>
-static cudaError_t project_t(const QrParams& P, const GEntry* tab, const uint8_t* first, const void* S,
-                             double2* partial, int i_lo, int i_hi, cudaStream_t st)
+static cudaError_t paths_t(const QrParams& P, const GEntry* tab, const uint8_t* first, const void* packed,
+                           long long row_stride, void* S, int i_lo, int i_hi, unsigned long long* counters,
+                           unsigned* status, cudaStream_t st)
 {
-    constexpr int BS = sizeof(R) == 4 ? kBS32 : kBS64;
+    if (sizeof(R) == 4 && paths_smem<R>(P, row_stride, D, kBS32) <= 227 * 1024)
+        return paths_bs<R, D, kBS32>(P, tab, first, packed, row_stride, S, i_lo, i_hi, counters, status, st);
+    return paths_bs<R, D, kBS64>(P, tab, first, packed, row_stride, S, i_lo, i_hi, counters, status, st);
+}
+
+template <typename R, int D, int BS>
+static cudaError_t project_bs(const QrParams& P, const GEntry* tab, const uint8_t* first, const void* S,
+                              double2* partial, int i_lo, int i_hi, cudaStream_t st)
+{
     constexpr int W = BS / 32;
     const size_t base = align16((size_t)P.nGp * sizeof(GEntry)) + align16((size_t)P.nGp) +
                         (size_t)D * P.K1 * BS * sizeof(V2<R>);
@@ -551,6 +566,17 @@ static cudaError_t project_t(const QrParams& P, const GEntry* tab, const uint8_t
     if (blocks <= 0) return cudaSuccess;
     kern<<<(unsigned)blocks, BS, sm, st>>>(P, tab, first, static_cast<const R*>(S), partial, i_lo, KT);
     return cudaGetLastError();
+}
+
+template <typename R, int D>
+static cudaError_t project_t(const QrParams& P, const GEntry* tab, const uint8_t* first, const void* S,
+                             double2* partial, int i_lo, int i_hi, cudaStream_t st)
+{
+    const size_t base32 = align16((size_t)P.nGp * sizeof(GEntry)) + align16((size_t)P.nGp) +
+                          (size_t)D * P.K1 * kBS32 * sizeof(V2<R>) + (kBS32 / 32) * 64 * sizeof(V2<R>);
+    if (sizeof(R) == 4 && base32 <= 227 * 1024)
+        return project_bs<R, D, kBS32>(P, tab, first, S, partial, i_lo, i_hi, st);
+    return project_bs<R, D, kBS64>(P, tab, first, S, partial, i_lo, i_hi, st);
 }
 
 template <typename R, int D>

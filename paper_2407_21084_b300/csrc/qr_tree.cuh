@@ -47,9 +47,9 @@ __device__ __forceinline__ void cfma(V2<R>& t, V2<R> c, V2<R> w)
 // converted once to R (no FP64 instruction per step in the FP32 form)
 template <typename R, int D>
 struct StepConsts {
-    R dt, sqdt, Lc, fc, glam, gkap, flam, fkap;
+    R dt, sqdt, Lc, fc, glam, gkap, flam, fkap, qh;
     R b[D], sig[D * D], fs[D], gs[D];
-    bool clamp, sig_diag;
+    bool clamp, sig_diag, damp;
     __device__ __forceinline__ explicit StepConsts(const QrParams& P)
     {
         dt = (R)P.dt;
@@ -62,6 +62,8 @@ struct StepConsts {
         glam = (R)P.g_lam;
         gkap = (R)P.g_kap;
         sig_diag = P.sig_diag != 0;
+        damp = P.q_damp != 0.0;
+        qh = (R)(0.5 * P.q_damp);
 #pragma unroll
         for (int l = 0; l < D; ++l) {
             b[l] = (R)P.b[l];
@@ -338,13 +340,14 @@ __device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __res
     }
 
     const StepConsts<R, D> K(Pm);
-    R x[P][D], sum[P], comp[P], gN[P];
+    R x[P][D], sum[P], comp[P], gN[P], lw0[P];
     unsigned long long hits = 0;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         V2<R> unused[D];
         start_point<R, D>(Pm, i, m0 + p * BS, x[p], unused, false);
         sum[p] = comp[p] = gN[p] = 0;
+        lw0[p] = K.damp ? damp_logw<R, D>(K.qh, x[p]) : (R)0;  // log w(X_i^i), eq. (yqi)
     }
     const R dt = K.dt;
 
@@ -385,6 +388,10 @@ __device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __res
 #pragma unroll
                 for (int l = 0; l < D; ++l) zz[p][l] = nu_phase<R>(Pm, x1[p][l]);
             tree_series<R, D, NN, KIND, P>(abuf[buf], zz, y);
+            if (K.damp && row < N) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) y[p] = undamp<R>(y[p], damp_logw<R, D>(K.qh, x1[p]));
+            }
             if (row < N && K.clamp) {
                 const R Lc = K.Lc;
 #pragma unroll
@@ -420,7 +427,7 @@ __device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __res
     for (int p = 0; p < P; ++p) {
         const long long m = m0 + p * BS;
         if (m < Pm.M) {
-            const R Sv = gN[p] + sum[p];
+            const R Sv = K.damp ? (gN[p] + sum[p]) * (R)exp((double)-lw0[p]) : gN[p] + sum[p];
             S[(size_t)(i - i_lo) * (size_t)Pm.M + (size_t)m] = Sv;
             if (!isfinite(Sv)) ++bad;
         }

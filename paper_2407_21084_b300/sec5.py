@@ -3,7 +3,7 @@
 Test problem: dX = dW, g = 1 + kappa + sin(lam sum x), f = min(1, [y - kappa
 - 1 - sin(lam sum x) e^{lam^2 d (t-T)/2}]^2), kappa = 0.6, lam = 1/sqrt(d),
 T = 1, Student nu (mu = 2), cosine basis on Gamma_F (d = 1), Gamma_T or
-Gamma_H, no damping (q = 0), one backward sweep (Algorithm 1) in FP32 as in
+Gamma_H, damping exponents q of eq. (yqi), one backward sweep (Algorithm 1) in FP32 as in
 the paper. For each timed row of the paper's tables that fits the generic
 kernels on one GPU, prints one JSON line with
 
@@ -12,8 +12,9 @@ kernels on one GPU, prints one JSON line with
   FP32, CUDA 7.5), and W = M |Gamma| N(N+1)/2 path.coef evaluations per
   second for both;
 * MSE_max and MSE_av of eq. (mse) against the exact solution (1000 test
-  points per time index), averaged over `--runs` independent runs, beside
-  the paper's q = 0 values (averages over 10^3 runs);
+  points per time index; damped by (1 + |x|^2)^{q/2} for q > 0), averaged
+  over `--runs` independent runs, for each damping exponent q the paper
+  tabulates, beside the paper's values (averages over 10^3 runs);
 * for the d = 1 rows with a printed interval: the 99 % confidence interval
   of ybar_0(0) over 50 runs beside the paper's (u(0,0) = 1.6).
 
@@ -30,25 +31,28 @@ import numpy as np
 from . import _lib as L
 from . import workloads as W
 
-# (label, d, kind, DEG or K, |Gamma|, Delta, M, paper GPU s, paper MSE_max, MSE_av at q = 0, paper 99 % CI)
+# (label, d, kind, DEG or K, |Gamma|, Delta, M, paper GPU s, paper (MSE_max, MSE_av) by damping q, paper 99 % CI)
 ROWS = [
-    ("d1 K=100", 1, W.G_FULL_N, 100, 101, 0.05, 2 * 10 ** 4, 0.09, -3.658, -3.868, (1.578, 1.667)),
-    ("d1 K=150", 1, W.G_FULL_N, 150, 151, 0.02, 2 * 10 ** 5, 7.37, -4.427, -4.900, (1.595, 1.624)),
-    ("d1 K=200", 1, W.G_FULL_N, 200, 201, 0.01, 2 * 10 ** 6, 414.44, -4.704, -5.524, None),
-    ("d2 Tot DEG20", 2, W.G_TOTAL_N, 20, 231, 0.05, 2 * 10 ** 4, 0.33, -2.322, -2.773, None),
-    ("d2 Tot DEG25", 2, W.G_TOTAL_N, 25, 351, 0.02, 2 * 10 ** 5, 35.51, -2.869, -3.688, None),
-    ("d2 Tot DEG31", 2, W.G_TOTAL_N, 31, 528, 0.01, 2 * 10 ** 6, 2243.06, -2.978, -3.966, None),
-    ("d2 Hyp DEG19", 2, W.G_HYP_N, 19, 99, 0.05, 2 * 10 ** 4, 0.16, -2.526, -3.062, None),
-    ("d2 Hyp DEG24", 2, W.G_HYP_N, 24, 133, 0.02, 2 * 10 ** 5, 12.38, -2.745, -3.550, None),
-    ("d2 Hyp DEG30", 2, W.G_HYP_N, 30, 172, 0.01, 2 * 10 ** 6, 662.54, -2.898, -3.770, None),
-    ("d3 Tot DEG22", 3, W.G_TOTAL_N, 22, 2300, 0.05, 2 * 10 ** 5, 53.89, -2.164, -2.785, None),
-    ("d3 Hyp DEG20", 3, W.G_HYP_N, 20, 411, 0.05, 2 * 10 ** 5, 8.37, -2.255, -3.191, None),
-    ("d3 Hyp DEG22", 3, W.G_HYP_N, 22, 459, 0.02, 2 * 10 ** 6, 592.19, -2.249, -3.356, None),
+    ("d1 K=100", 1, W.G_FULL_N, 100, 101, 0.05, 2 * 10 ** 4, 0.09,
+     {0.0: (-3.658, -3.868), 2.1: (-4.615, -4.874), 5.1: (-4.517, -5.130), 8.1: (-4.781, -5.319)}, (1.578, 1.667)),
+    ("d1 K=150", 1, W.G_FULL_N, 150, 151, 0.02, 2 * 10 ** 5, 7.37,
+     {0.0: (-4.427, -4.900), 2.1: (-6.450, -6.740), 5.1: (-6.685, -7.094), 8.1: (-6.740, -7.221)}, (1.595, 1.624)),
+    ("d1 K=200", 1, W.G_FULL_N, 200, 201, 0.01, 2 * 10 ** 6, 414.44,
+     {0.0: (-4.704, -5.524), 2.1: (-8.465, -8.729), 5.1: (-8.717, -9.096), 8.1: (-8.830, -9.301)}, None),
+    ("d2 Tot DEG20", 2, W.G_TOTAL_N, 20, 231, 0.05, 2 * 10 ** 4, 0.33, {0.0: (-2.322, -2.773), 5.1: (-4.646, -5.239)}, None),
+    ("d2 Tot DEG25", 2, W.G_TOTAL_N, 25, 351, 0.02, 2 * 10 ** 5, 35.51, {0.0: (-2.869, -3.688), 5.1: (-6.761, -7.186)}, None),
+    ("d2 Tot DEG31", 2, W.G_TOTAL_N, 31, 528, 0.01, 2 * 10 ** 6, 2243.06, {0.0: (-2.978, -3.966), 5.1: (-8.793, -9.107)}, None),
+    ("d2 Hyp DEG19", 2, W.G_HYP_N, 19, 99, 0.05, 2 * 10 ** 4, 0.16, {0.0: (-2.526, -3.062), 5.1: (-5.588, -6.196)}, None),
+    ("d2 Hyp DEG24", 2, W.G_HYP_N, 24, 133, 0.02, 2 * 10 ** 5, 12.38, {0.0: (-2.745, -3.550), 5.1: (-7.487, -8.191)}, None),
+    ("d2 Hyp DEG30", 2, W.G_HYP_N, 30, 172, 0.01, 2 * 10 ** 6, 662.54, {0.0: (-2.898, -3.770), 5.1: (-9.389, -10.137)}, None),
+    ("d3 Tot DEG22", 3, W.G_TOTAL_N, 22, 2300, 0.05, 2 * 10 ** 5, 53.89, {0.0: (-2.164, -2.785), 5.1: (-5.699, -6.141)}, None),
+    ("d3 Hyp DEG20", 3, W.G_HYP_N, 20, 411, 0.05, 2 * 10 ** 5, 8.37, {0.0: (-2.255, -3.191), 5.1: (-6.883, -7.662)}, None),
+    ("d3 Hyp DEG22", 3, W.G_HYP_N, 22, 459, 0.02, 2 * 10 ** 6, 592.19, {0.0: (-2.249, -3.356), 5.1: (-7.778, -8.875)}, None),
 ]
 
 
-def _problem(d, kind, n, delta, M, seed):
-    return W.Sec5Problem(d=d, N=int(round(1.0 / delta)), gamma_kind=kind, gamma_n=n, M=M, seed=seed)
+def _problem(d, kind, n, delta, M, seed, q=0.0):
+    return W.Sec5Problem(d=d, N=int(round(1.0 / delta)), gamma_kind=kind, gamma_n=n, M=M, seed=seed, q=q)
 
 
 def run_row(row, runs: int, ci_runs: int, precision=L.QR_FP32):
@@ -56,19 +60,25 @@ def run_row(row, runs: int, ci_runs: int, precision=L.QR_FP32):
 
     from .solver import Solver
 
-    label, d, kind, n, ng, delta, M, gpu_s, mmax, mav, ci = row
-    times, mse = [], []
-    for r in range(runs):
-        p = _problem(d, kind, n, delta, M, seed=1 + r)
-        with Solver.from_sec5(p, precision=precision) as s:
-            k, _ = s.cosine_coefs()
-            assert len(k) == ng, (label, len(k), ng)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            s.backward_sweep()
-            torch.cuda.synchronize()
-            times.append(time.perf_counter() - t0)
-            mse.append(s.mse_indicators(lambda t, x: p.exact_u(t, x), n=1000))
+    label, d, kind, n, ng, delta, M, gpu_s, paper_mse, ci = row
+    times, mse = [], {}
+    for q in paper_mse:
+        per = []
+        for r in range(runs):
+            p = _problem(d, kind, n, delta, M, seed=1 + r, q=q)
+            with Solver.from_sec5(p, precision=precision) as s:
+                k, _ = s.cosine_coefs()
+                assert len(k) == ng, (label, len(k), ng)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                s.backward_sweep()
+                torch.cuda.synchronize()
+                if q == 0.0:
+                    times.append(time.perf_counter() - t0)
+                per.append(s.mse_indicators(lambda t, x: p.exact_u(t, x), n=1000))
+        mse[str(q)] = {"mse_max": float(np.mean([m["mse_max"] for m in per])),
+                       "mse_av": float(np.mean([m["mse_av"] for m in per])),
+                       "paper_mse_max": paper_mse[q][0], "paper_mse_av": paper_mse[q][1]}
     N = int(round(1.0 / delta))
     work = float(M) * ng * N * (N + 1) / 2.0
     t = float(np.median(times))
@@ -77,8 +87,7 @@ def run_row(row, runs: int, ci_runs: int, precision=L.QR_FP32):
            "s_per_sweep": t, "evals_per_s": work / t,
            "paper_gpu_s": gpu_s, "paper_gpu_evals_per_s": work / gpu_s, "speedup_vs_paper_gpu": gpu_s / t,
            "paper_hardware": "1x GeForce GTX TITAN Black (Kepler GK110), FP32, CUDA 7.5",
-           "mse_max": float(np.mean([m["mse_max"] for m in mse])), "mse_av": float(np.mean([m["mse_av"] for m in mse])),
-           "paper_mse_max_q0": mmax, "paper_mse_av_q0": mav, "runs": runs}
+           "mse_by_q": mse, "runs": runs}
     if ci is not None and ci_runs > 0:
         vals = []
         for r in range(ci_runs):

@@ -21,7 +21,8 @@ class Solver:
     """A QRMC problem on the GPU (wraps a qr_ctx)."""
 
     def __init__(self, d, N, T, nu_kind, mu, gamma_kind, gamma_n, b, sigma, f_kind, f_par, g_kind, g_par, M,
-                 seed, precision=L.QR_FP64, clamp_L=0.0, stream=None, lattice_n=0, instance=0, path_kernel=0):
+                 seed, precision=L.QR_FP64, clamp_L=0.0, stream=None, lattice_n=0, instance=0, path_kernel=0,
+                 damping_q=0.0):
         self._L = L.load()
         self.d, self.N, self.T, self.M = int(d), int(N), float(T), int(M)
         self.precision = precision
@@ -47,8 +48,10 @@ class Solver:
                 stream_ptr = None
         else:
             stream_ptr = stream
+        self.damping_q = float(damping_q)
         opts = L.QrOpts(M, seed, precision, clamp_L, stream_ptr,
-                        L.QR_U_LATTICE if lattice_n else L.QR_U_PHILOX, lattice_n, instance, path_kernel)
+                        L.QR_U_LATTICE if lattice_n else L.QR_U_PHILOX, lattice_n, instance, path_kernel,
+                        self.damping_q)
         self._ctx = C.c_void_p()
         st = self._L.qr_init(C.byref(self._ctx), d, N, T, C.byref(nu), C.byref(gam), _dp(b), _dp(sigma),
                              C.byref(f), C.byref(g), C.byref(opts))
@@ -70,10 +73,11 @@ class Solver:
     @classmethod
     def from_sec5(cls, p: Sec5Problem, precision=L.QR_FP64, M=None, stream=None, instance=0, path_kernel=0):
         """The test problem of Sec. 5 (Student nu, min/sin driver and terminal
-        condition, cosine basis), no truncation."""
+        condition, cosine basis, damping exponent p.q), no truncation."""
         return cls(p.d, p.N, p.T, L.QR_NU_STUDENT2, 2.0, p.gamma_kind, p.gamma_n, p.b, p.sigma,
                    L.QR_F_PAPER_MIN, p.f_par, L.QR_GT_PAPER_SIN, p.g_par, p.M if M is None else M, p.seed,
-                   precision=precision, clamp_L=0.0, stream=stream, instance=instance, path_kernel=path_kernel)
+                   precision=precision, clamp_L=0.0, stream=stream, instance=instance, path_kernel=path_kernel,
+                   damping_q=p.q)
 
     def cosine_coefs(self):
         """For a context of the cosine basis (N^d set): the N^d multi-indices
@@ -140,11 +144,15 @@ class Solver:
 
     def mse_indicators(self, exact, n: int = 1000) -> dict:
         """MSE_max and MSE_av of Sec. 5, eq. (mse): natural logs of the mean
-        squared error of ybar_i against exact(t_i, x) at n test points per i."""
+        squared error of ybar_i against exact(t_i, x) at n test points per i
+        (with damping, of the damped ybar^q_i against exact / (1 + |x|^2)^{q/2})."""
         per_i = []
         for i in range(self.N):
             x = self.test_points(i, n)
-            e = self.eval(i, x) - exact(i * self.T / self.N, x)
+            ex = exact(i * self.T / self.N, x)
+            if self.damping_q:
+                ex = ex / (1.0 + (x * x).sum(axis=1)) ** (self.damping_q / 2)
+            e = self.eval(i, x) - ex
             per_i.append(float(np.mean(e * e)))
         per_i = np.array(per_i)
         return {"mse_max": float(np.log(per_i.max())), "mse_av": float(np.log(per_i.mean())), "points": n}

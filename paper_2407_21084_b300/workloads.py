@@ -152,7 +152,8 @@ class Sec5Problem:
     g = 1 + kappa + sin(lam sum x), f = min(1, [y - kappa - 1 - sin(lam sum x)
     e^{lam^2 d (t-T)/2}]^2), exact solution u = 1 + kappa + sin(lam sum x)
     e^{lam^2 d (t-T)/2}; kappa = 0.6, lam = 1/sqrt(d), T = 1; Student nu with
-    mu = 2; cosine basis on an N^d set (Gamma_F, Gamma_T or Gamma_H)."""
+    mu = 2; cosine basis on an N^d set (Gamma_F, Gamma_T or Gamma_H); damping
+    exponent q of eq. (yqi)."""
 
     d: int
     N: int
@@ -162,6 +163,7 @@ class Sec5Problem:
     seed: int
     T: float = 1.0
     kappa: float = 0.6
+    q: float = 0.0  # damping exponent of eq. (yqi)
 
     @property
     def lam(self) -> float:
@@ -188,9 +190,9 @@ class Sec5Problem:
         return 1.0 + self.kappa + np.sin(self.lam * sx) * np.exp(self.lam ** 2 * self.d * (t - self.T) / 2.0)
 
 
-def sec5_d1(K: int, N: int, M: int, seed: int) -> Sec5Problem:
+def sec5_d1(K: int, N: int, M: int, seed: int, q: float = 0.0) -> Sec5Problem:
     """d = 1 rows of the paper's Sec. 5 (Delta = 1/N, K + 1 cosines, M paths)."""
-    return Sec5Problem(d=1, N=N, gamma_kind=G_FULL_N, gamma_n=K, M=M, seed=seed)
+    return Sec5Problem(d=1, N=N, gamma_kind=G_FULL_N, gamma_n=K, M=M, seed=seed, q=q)
 
 
 CONFIGS = {"c1": c1, "c2": c2, "c3": c3}

@@ -108,3 +108,25 @@ def test_paper_d1_confidence_interval(mods):
     lo, hi = v.mean() - half, v.mean() + half
     assert lo <= 1.6 <= hi, (lo, hi)
     assert lo <= 1.667 and hi >= 1.578, (lo, hi)
+
+
+@pytest.mark.parametrize("d,kind,n,N,M,q", [
+    (1, W.G_FULL_N, 40, 5, 3000, 5.1),
+    (2, W.G_TOTAL_N, 6, 4, 2500, 2.1),
+    (2, W.G_HYP_N, 7, 4, 2500, 8.1),
+    (6, W.G_TOTAL_N, 5, 3, 1100, 5.1),   # compile-time tree kernels with the damping weights
+])
+def test_damped_picard_matches_oracle(mods, ora, d, kind, n, N, M, q):
+    """Damping exponent q of eq. (yqi) in the responses of eq. (Sqi:bar:M)."""
+    solver = mods
+    p = W.Sec5Problem(d=d, N=N, gamma_kind=kind, gamma_n=n, M=M, seed=13, q=q)
+    op = _oracle_problem(ora, p)
+    op.q_damp = q
+    ref, _ = ora.picard(op, 2)
+    ref = ref.real
+    for prec, tol in ((0, 1e-10), (1, 1e-4)):
+        with solver.Solver.from_sec5(p, precision=prec) as s:
+            s.picard_step(2)
+            _, a = s.cosine_coefs()
+        err = np.abs(a - ref).max() / np.abs(ref).max()
+        assert err < tol, (prec, err)
