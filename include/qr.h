@@ -210,6 +210,16 @@ void qr_destroy(qr_ctx* ctx);
  * MSE over 10^3 nu-points per time index. */
 qr_status qr_test_points(const qr_ctx* ctx, int i, long long n, double* x_out);
 
+/* Test hook (the paper has no counterpart): runs, on the context's stream,
+ * one kernel whose bounded mbarrier wait cannot complete (an expected
+ * transaction with no copy behind it). The wait gives up after about 2^31
+ * SM cycles (~1 s), the kernel records the timeout in the context's status
+ * word and returns, and this call returns QR_ETIMEOUT with the message of a
+ * timed-out wait, exactly as a Picard step would. The status word is then
+ * cleared: the context stays usable. Any other status is a failure of the
+ * mechanism. */
+qr_status qr_selftest_wait_timeout(qr_ctx* ctx);
+
 /* ---- many instances in one iteration ----------------------------------
  * A batch advances n contexts (created by qr_init with QR_FP32, sharing one
  * stream, each with one of the compiled index-set classes: |k|_inf <= 4 in

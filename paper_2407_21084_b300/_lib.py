@@ -26,6 +26,7 @@ EXPORTS = [
     "qr_init", "qr_picard_step", "qr_backward_sweep", "qr_eval", "qr_gamma_size", "qr_gamma_list",
     "qr_get_coefs", "qr_set_coefs", "qr_get_responses", "qr_set_profiling", "qr_get_stats",
     "qr_last_error", "qr_status_string", "qr_destroy", "qr_philox_words", "qr_sample", "qr_project_static", "qr_test_points",
+    "qr_selftest_wait_timeout",
     "qr_mlp_create", "qr_mlp_num_params", "qr_mlp_get_params", "qr_mlp_set_params", "qr_mlp_forward",
     "qr_mlp_gradients", "qr_mlp_train_step", "qr_mlp_last_error", "qr_mlp_destroy",
     "qr_batch_create", "qr_batch_picard_step", "qr_batch_info", "qr_batch_set_grouping", "qr_batch_groups",
@@ -153,6 +154,8 @@ def load(path: str | None = None):
     L.qr_batch_picard_step.argtypes = [vp, C.c_int, dp]
     L.qr_batch_info.restype = C.c_int
     L.qr_batch_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
+    L.qr_selftest_wait_timeout.restype = C.c_int
+    L.qr_selftest_wait_timeout.argtypes = [vp]
     L.qr_batch_set_grouping.restype = C.c_int
     L.qr_batch_set_grouping.argtypes = [vp, C.c_int]
     L.qr_batch_groups.restype = C.c_int

@@ -733,6 +733,17 @@ qr_status qr_picard_step(qr_ctx* ctx, int n_iter, double* residual_out)
     return QR_OK;
 }
 
+qr_status qr_selftest_wait_timeout(qr_ctx* ctx)
+{
+    if (!ready(ctx)) return QR_EINVAL;
+    QR_CU(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
+    QR_CU(ctx, launch_wait_selftest(ctx->d_status, ctx->stream));
+    const qr_status s = check_device_status(ctx);
+    QR_CU(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
+    QR_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return s;
+}
+
 qr_status qr_backward_sweep(qr_ctx* ctx)
 {
     if (!ready(ctx)) return QR_EINVAL;

@@ -82,6 +82,8 @@ cudaError_t launch_reduce(int prec, const QrParams& P, const double2* partial, d
                           unsigned long long* counters, cudaStream_t st);
 cudaError_t launch_pack(int prec, const QrParams& P, const double2* alpha, int nG, int zero_idx,
                         void* packed, long long row_stride, int rows, cudaStream_t st);
+// a bounded wait that runs out on purpose (status |= ST_TIMEOUT after ~1 s)
+cudaError_t launch_wait_selftest(unsigned* status, cudaStream_t st);
 // cosine basis: symmetrise the raw projections of rows [i_lo, i_hi) over the
 // sign orbits (CSR orb_off/orb_idx over the canonical Z^d order) into alpha
 cudaError_t launch_sym_cos(const double2* raw, double2* alpha, int nG, const int* orb_off, const int* orb_idx,

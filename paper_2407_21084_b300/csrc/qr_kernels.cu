@@ -718,4 +718,30 @@ cudaError_t launch_sym_cos(const double2* raw, double2* alpha, int nG, const int
     return cudaGetLastError();
 }
 
+// Test of the bounded waits: one arrival with 16 bytes of expected
+// transaction and no copy behind it, so the barrier phase never completes;
+// the bounded wait gives up (~2^31 cycles), the status word records the
+// timeout and the kernel returns. No copy is in flight when it exits.
+__global__ void k_wait_selftest(unsigned* __restrict__ status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)), "r"(16u)
+                     : "memory");
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0u);
+    if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+}
+
+cudaError_t launch_wait_selftest(unsigned* status, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(status);
+    return cudaGetLastError();
+}
+
 }  // namespace qr
