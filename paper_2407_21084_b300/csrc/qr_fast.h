@@ -36,4 +36,12 @@ int proj_tree_nodes_more(int kind, int d, int n);
 cudaError_t launch_project_tree_more(int prec, int kind, int n, const QrParams& P, const void* S, const int* perm,
                                      double2* partial, int i_lo, int i_hi, cudaStream_t st);
 
+// path kernels for the sets of the paper's own experiments (qr_fast_paper.cu),
+// reached through the above; their projections use the table kernel (a
+// compile-time projection of these long chains takes too long to build)
+int tree_slots_paper(int kind, int d, int n);
+cudaError_t launch_paths_tree_paper(int prec, int kind, int n, const QrParams& P, const void* tree,
+                                    long long row_stride, void* S, int i_lo, int i_hi, unsigned long long* counters,
+                                    unsigned* status, cudaStream_t st);
+
 }  // namespace qr

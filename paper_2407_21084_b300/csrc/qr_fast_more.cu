@@ -19,7 +19,7 @@ int tree_slots_more(int kind, int d, int n)
     if (kind == K && d == DD && n == NNN) return tree_slots_t<DD, NNN, K>();
     QR_TREE_MORE(QR_X)
 #undef QR_X
-    return 0;
+    return tree_slots_paper(kind, d, n);
 }
 
 cudaError_t launch_paths_tree_more(int prec, int kind, int n, const QrParams& P, const void* tree,
@@ -33,7 +33,7 @@ cudaError_t launch_paths_tree_more(int prec, int kind, int n, const QrParams& P,
                    : paths_tree_t<double, DD, NNN, K>(P, tree, row_stride, S, i_lo, i_hi, counters, status, st);
     QR_TREE_MORE(QR_X)
 #undef QR_X
-    return cudaErrorInvalidValue;
+    return launch_paths_tree_paper(prec, kind, n, P, tree, row_stride, S, i_lo, i_hi, counters, status, st);
 }
 
 }  // namespace qr

@@ -108,7 +108,7 @@ def main():
     ap.add_argument("--rows", default="d1,d2,d3", help="comma-separated prefixes of the row labels")
     ap.add_argument("--runs", type=int, default=3, help="independent runs per row for time and MSE")
     ap.add_argument("--ci-runs", type=int, default=50, help="runs for the d = 1 confidence intervals")
-    ap.add_argument("--max-gpu-s", type=float, default=1000.0, help="skip rows the paper timed above this")
+    ap.add_argument("--max-gpu-s", type=float, default=3000.0, help="skip rows the paper timed above this")
     args = ap.parse_args()
     want = [w.strip() for w in args.rows.split(",") if w.strip()]
     for row in ROWS:
