@@ -153,10 +153,11 @@ bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vect
     auto pair = [&](const std::vector<int>& kp, const std::vector<int>& km) {
         const int ep = std::max(find(kp), 0), em = std::max(find(km), 0);
         if (find(kp) < 0 || find(km) < 0) ok = false;
+        // slots (A, C) and (B, E): T += (A, C) (z.x, z.y) + (B, E) (z.y, z.x)
         TreeMap a{}, b{};
         a.i[0][0] = 2 * ep; a.c[0][0] = 2.0; a.i[0][1] = 2 * em; a.c[0][1] = 2.0;           // A = a+ + a-
-        a.i[1][0] = 2 * em + 1; a.c[1][0] = 2.0; a.i[1][1] = 2 * ep + 1; a.c[1][1] = -2.0;  // B = b- - b+
-        b.i[0][0] = 2 * ep; b.c[0][0] = 2.0; b.i[0][1] = 2 * em; b.c[0][1] = -2.0;          // C = a+ - a-
+        a.i[1][0] = 2 * ep; a.c[1][0] = 2.0; a.i[1][1] = 2 * em; a.c[1][1] = -2.0;          // C = a+ - a-
+        b.i[0][0] = 2 * em + 1; b.c[0][0] = 2.0; b.i[0][1] = 2 * ep + 1; b.c[0][1] = -2.0;  // B = b- - b+
         b.i[1][0] = 2 * ep + 1; b.c[1][0] = 2.0; b.i[1][1] = 2 * em + 1; b.c[1][1] = 2.0;   // E = b+ + b-
         out.push_back(a);
         out.push_back(b);

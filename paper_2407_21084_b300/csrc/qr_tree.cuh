@@ -160,6 +160,12 @@ __device__ __forceinline__ R term_g_fast(const QrParams& P, const StepConsts<R, 
     return (R)1 + K.gkap + rsin<R>(K.glam * sx);
 }
 
+// +-1 leaf pairs of the FP32 form as two packed two-lane FMA per path
+// (__ffma2_rn: the same roundings as four scalar FMA, half the issue slots)
+#ifndef QR_TREE_PAIR2
+#define QR_TREE_PAIR2 1
+#endif
+
 // subtrees of at most this many slots have both signs unrolled
 #ifndef QR_TREE_UNROLL
 #define QR_TREE_UNROLL 8
@@ -194,15 +200,24 @@ struct NewDims {
         if constexpr (L2 < D) {
             constexpr int S2 = Sh::new_S(S);
             if constexpr (Sh::leaf(L2, S2)) {
-                // T += c+ z + c- conj(z), pre-combined as (A, B), (C, E):
-                // T.x += A z.x + B z.y,  T.y += C z.y + E z.x
-                const V2<R> ab = c[off], ce = c[off + 1];
+                // T += c+ z + c- conj(z), pre-combined as the slots (A, C), (B, E):
+                // T.x += A z.x + B z.y,  T.y += C z.y + E z.x, i.e.
+                // T += (A, C) * (z.x, z.y) + (B, E) * (z.y, z.x) lane-wise
+                const V2<R> ac = c[off], be = c[off + 1];
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    T[p].x = fma(ab.x, z[p][L2].x, T[p].x);
-                    T[p].x = fma(ab.y, z[p][L2].y, T[p].x);
-                    T[p].y = fma(ce.x, z[p][L2].y, T[p].y);
-                    T[p].y = fma(ce.y, z[p][L2].x, T[p].y);
+#if QR_TREE_PAIR2
+                    if constexpr (sizeof(R) == 4) {
+                        const float2 zl = z[p][L2];
+                        T[p] = __ffma2_rn(ac, zl, T[p]);
+                        T[p] = __ffma2_rn(be, make_float2(zl.y, zl.x), T[p]);
+                        continue;
+                    }
+#endif
+                    T[p].x = fma(ac.x, z[p][L2].x, T[p].x);
+                    T[p].x = fma(be.x, z[p][L2].y, T[p].x);
+                    T[p].y = fma(ac.y, z[p][L2].y, T[p].y);
+                    T[p].y = fma(be.y, z[p][L2].x, T[p].y);
                 }
                 off += 2;
             } else {
