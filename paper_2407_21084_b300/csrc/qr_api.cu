@@ -469,7 +469,8 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
         // powers z_l^a, a <= max|k_l|, of every lane in shared memory
         const size_t v2 = o.precision == QR_FP32 ? sizeof(float2) : sizeof(double2);
         const size_t nGp = (size_t)(c->nG - (c->nG - 1) / 2);
-        const size_t need = (size_t)d * (c->kmax + 1) * 128 * v2 + 2 * nGp * v2 + nGp * (sizeof(GEntry) + 1) + 256;
+        // (the index table itself moves to global memory when it does not fit)
+        const size_t need = (size_t)d * (c->kmax + 1) * 128 * v2 + 2 * nGp * v2 + 256;
         if (need > 227 * 1024)
             return bail(QR_ENOTIMPL, "index set too large for the table kernels: " + std::to_string(need / 1024) +
                                          " KB of shared memory per block (limit 227 KB)");

@@ -100,7 +100,10 @@ __device__ __forceinline__ T warp_sum(T v)
 }
 
 // ------------------------------------------------------ path-and-series kernel
-template <typename R, int D, int BS>
+// TG: the table of multi-indices is read from global memory (warp-uniform,
+// L1-cached loads) instead of being copied to shared memory, for index sets
+// whose table would not leave room for the power tables and coefficient rows
+template <typename R, int D, int BS, bool TG>
 __global__ void __launch_bounds__(BS) k_paths(const __grid_constant__ QrParams P, const GEntry* __restrict__ gtab,
                                               const uint8_t* __restrict__ gfirst,
                                               const V2<R>* __restrict__ packed, long long row_stride,
@@ -112,10 +115,12 @@ __global__ void __launch_bounds__(BS) k_paths(const __grid_constant__ QrParams P
     const int nGp = P.nGp, K1 = P.K1, N = P.N;
     const uint32_t rowbytes = (uint32_t)(row_stride * sizeof(V2<R>));
     size_t off = 0;
-    GEntry* tab = reinterpret_cast<GEntry*>(smem + off);
-    off += align16((size_t)nGp * sizeof(GEntry));
-    uint8_t* first = smem + off;
-    off += align16((size_t)nGp);
+    GEntry* stab = reinterpret_cast<GEntry*>(smem + off);
+    if (!TG) off += align16((size_t)nGp * sizeof(GEntry));
+    uint8_t* sfirst = smem + off;
+    if (!TG) off += align16((size_t)nGp);
+    const GEntry* tab = TG ? gtab : stab;
+    const uint8_t* first = TG ? gfirst : sfirst;
     V2<R>* abuf[2];
     abuf[0] = reinterpret_cast<V2<R>*>(smem + off);
     off += rowbytes;
@@ -131,10 +136,11 @@ __global__ void __launch_bounds__(BS) k_paths(const __grid_constant__ QrParams P
     const bool active = m < P.M;
     const bool trig = P.g_kind == QR_GT_TRIGPOLY;
 
-    for (int e = tid; e < nGp; e += BS) {
-        tab[e] = gtab[e];
-        first[e] = gfirst[e];
-    }
+    if (!TG)
+        for (int e = tid; e < nGp; e += BS) {
+            stab[e] = gtab[e];
+            sfirst[e] = gfirst[e];
+        }
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -254,7 +260,7 @@ __device__ __forceinline__ void start_phases(const QrParams& P, int i, long long
     for (int l = 0; l < D; ++l) ph[l] = u_phase<R>(n[l], P.half_angle != 0);
 }
 
-template <typename R, int D, int BS>
+template <typename R, int D, int BS, bool TG>
 __global__ void __launch_bounds__(BS) k_project(const __grid_constant__ QrParams P, const GEntry* __restrict__ gtab,
                                                 const uint8_t* __restrict__ gfirst, const R* __restrict__ S,
                                                 double2* __restrict__ partial, int i_lo, int KT)
@@ -263,10 +269,12 @@ __global__ void __launch_bounds__(BS) k_project(const __grid_constant__ QrParams
     constexpr int W = BS / 32;
     const int nGp = P.nGp, K1 = P.K1;
     size_t off = 0;
-    GEntry* tab = reinterpret_cast<GEntry*>(smem + off);
-    off += align16((size_t)nGp * sizeof(GEntry));
-    uint8_t* first = smem + off;
-    off += align16((size_t)nGp);
+    GEntry* stab = reinterpret_cast<GEntry*>(smem + off);
+    if (!TG) off += align16((size_t)nGp * sizeof(GEntry));
+    uint8_t* sfirst = smem + off;
+    if (!TG) off += align16((size_t)nGp);
+    const GEntry* tab = TG ? gtab : stab;
+    const uint8_t* first = TG ? gfirst : sfirst;
     V2<R>* pw = reinterpret_cast<V2<R>*>(smem + off);
     off += (size_t)D * K1 * BS * sizeof(V2<R>);
     V2<R>* acc = reinterpret_cast<V2<R>*>(smem + off);
@@ -274,10 +282,11 @@ __global__ void __launch_bounds__(BS) k_project(const __grid_constant__ QrParams
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int i = i_lo + (int)(blockIdx.x / P.n_chunks);
     const int ch = (int)(blockIdx.x % P.n_chunks);
-    for (int e = tid; e < nGp; e += BS) {
-        tab[e] = gtab[e];
-        first[e] = gfirst[e];
-    }
+    if (!TG)
+        for (int e = tid; e < nGp; e += BS) {
+            stab[e] = gtab[e];
+            sfirst[e] = gfirst[e];
+        }
     V2<R>* mypw = pw + tid;
     const int rounds = P.chunk / BS;
 
@@ -413,7 +422,7 @@ __global__ void k_pack(const double2* __restrict__ alpha, int nG, int zero_idx, 
 }
 
 // ------------------------------------------------------------ evaluation
-template <typename R, int D, int BS>
+template <typename R, int D, int BS, bool TG>
 __global__ void __launch_bounds__(BS) k_eval(const __grid_constant__ QrParams P, const GEntry* __restrict__ gtab,
                                              const uint8_t* __restrict__ gfirst, const V2<R>* __restrict__ crow,
                                              const double* __restrict__ xs, long long n, double* __restrict__ ys,
@@ -422,17 +431,21 @@ __global__ void __launch_bounds__(BS) k_eval(const __grid_constant__ QrParams P,
     extern __shared__ __align__(16) unsigned char smem[];
     const int nGp = P.nGp, K1 = P.K1;
     size_t off = 0;
-    GEntry* tab = reinterpret_cast<GEntry*>(smem + off);
-    off += align16((size_t)nGp * sizeof(GEntry));
-    uint8_t* first = smem + off;
-    off += align16((size_t)nGp);
+    GEntry* stab = reinterpret_cast<GEntry*>(smem + off);
+    if (!TG) off += align16((size_t)nGp * sizeof(GEntry));
+    uint8_t* sfirst = smem + off;
+    if (!TG) off += align16((size_t)nGp);
+    const GEntry* tab = TG ? gtab : stab;
+    const uint8_t* first = TG ? gfirst : sfirst;
     V2<R>* coef = reinterpret_cast<V2<R>*>(smem + off);
     off += align16((size_t)nGp * sizeof(V2<R>));
     V2<R>* pw = reinterpret_cast<V2<R>*>(smem + off);
     const int tid = threadIdx.x;
     for (int e = tid; e < nGp; e += BS) {
-        tab[e] = gtab[e];
-        first[e] = gfirst[e];
+        if (!TG) {
+            stab[e] = gtab[e];
+            sfirst[e] = gfirst[e];
+        }
         if (!use_g) coef[e] = crow[e];
     }
     __syncthreads();
@@ -510,21 +523,26 @@ static cudaError_t test_points_t(const QrParams& P, int i, long long n, double* 
 // ------------------------------------------------------------ launchers
 constexpr int kBS32 = 256, kBS64 = 128;
 
-template <typename R>
-static size_t paths_smem(const QrParams& P, long long row_stride, int D, int BS)
+// bytes of the index table in shared memory (none when it stays in global memory)
+static size_t tab_smem(const QrParams& P, bool tg)
 {
-    return align16((size_t)P.nGp * sizeof(GEntry)) + align16((size_t)P.nGp) + 2 * (size_t)row_stride * sizeof(V2<R>) +
-           (size_t)D * P.K1 * BS * sizeof(V2<R>) + 16;
+    return tg ? 0 : align16((size_t)P.nGp * sizeof(GEntry)) + align16((size_t)P.nGp);
 }
 
-template <typename R, int D, int BS>
+template <typename R>
+static size_t paths_smem(const QrParams& P, long long row_stride, int D, int BS, bool tg)
+{
+    return tab_smem(P, tg) + 2 * (size_t)row_stride * sizeof(V2<R>) + (size_t)D * P.K1 * BS * sizeof(V2<R>) + 16;
+}
+
+template <typename R, int D, int BS, bool TG>
 static cudaError_t paths_bs(const QrParams& P, const GEntry* tab, const uint8_t* first, const void* packed,
                             long long row_stride, void* S, int i_lo, int i_hi, unsigned long long* counters,
                             unsigned* status, cudaStream_t st)
 {
-    const size_t sm = paths_smem<R>(P, row_stride, D, BS);
+    const size_t sm = paths_smem<R>(P, row_stride, D, BS, TG);
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
-    auto kern = k_paths<R, D, BS>;
+    auto kern = k_paths<R, D, BS, TG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int tiles = (int)((P.M + BS - 1) / BS);
@@ -536,30 +554,33 @@ static cudaError_t paths_bs(const QrParams& P, const GEntry* tab, const uint8_t*
 }
 
 // FP32 runs 256-thread blocks when their power tables fit in shared memory,
-// else 128 (long one-dimensional sets); FP64 always 128
+// else 128 (long one-dimensional sets); FP64 always 128; the index table
+// moves to global memory only when nothing else fits
 template <typename R, int D>
 static cudaError_t paths_t(const QrParams& P, const GEntry* tab, const uint8_t* first, const void* packed,
                            long long row_stride, void* S, int i_lo, int i_hi, unsigned long long* counters,
                            unsigned* status, cudaStream_t st)
 {
-    if (sizeof(R) == 4 && paths_smem<R>(P, row_stride, D, kBS32) <= 227 * 1024)
-        return paths_bs<R, D, kBS32>(P, tab, first, packed, row_stride, S, i_lo, i_hi, counters, status, st);
-    return paths_bs<R, D, kBS64>(P, tab, first, packed, row_stride, S, i_lo, i_hi, counters, status, st);
+    constexpr size_t cap = 227 * 1024;
+    if (sizeof(R) == 4 && paths_smem<R>(P, row_stride, D, kBS32, false) <= cap)
+        return paths_bs<R, D, kBS32, false>(P, tab, first, packed, row_stride, S, i_lo, i_hi, counters, status, st);
+    if (paths_smem<R>(P, row_stride, D, kBS64, false) <= cap)
+        return paths_bs<R, D, kBS64, false>(P, tab, first, packed, row_stride, S, i_lo, i_hi, counters, status, st);
+    return paths_bs<R, D, kBS64, true>(P, tab, first, packed, row_stride, S, i_lo, i_hi, counters, status, st);
 }
 
-template <typename R, int D, int BS>
+template <typename R, int D, int BS, bool TG>
 static cudaError_t project_bs(const QrParams& P, const GEntry* tab, const uint8_t* first, const void* S,
                               double2* partial, int i_lo, int i_hi, cudaStream_t st)
 {
     constexpr int W = BS / 32;
-    const size_t base = align16((size_t)P.nGp * sizeof(GEntry)) + align16((size_t)P.nGp) +
-                        (size_t)D * P.K1 * BS * sizeof(V2<R>);
+    const size_t base = tab_smem(P, TG) + (size_t)D * P.K1 * BS * sizeof(V2<R>);
     const size_t cap = 227 * 1024;
     if (base + W * sizeof(V2<R>) > cap) return cudaErrorInvalidConfiguration;
     int KT = (int)((cap - base) / (W * sizeof(V2<R>)));
     if (KT > P.nGp) KT = P.nGp;
     const size_t sm = base + (size_t)W * KT * sizeof(V2<R>);
-    auto kern = k_project<R, D, BS>;
+    auto kern = k_project<R, D, BS, TG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const long long blocks = (long long)P.n_chunks * (i_hi - i_lo);
@@ -572,28 +593,39 @@ template <typename R, int D>
 static cudaError_t project_t(const QrParams& P, const GEntry* tab, const uint8_t* first, const void* S,
                              double2* partial, int i_lo, int i_hi, cudaStream_t st)
 {
-    const size_t base32 = align16((size_t)P.nGp * sizeof(GEntry)) + align16((size_t)P.nGp) +
-                          (size_t)D * P.K1 * kBS32 * sizeof(V2<R>) + (kBS32 / 32) * 64 * sizeof(V2<R>);
-    if (sizeof(R) == 4 && base32 <= 227 * 1024)
-        return project_bs<R, D, kBS32>(P, tab, first, S, partial, i_lo, i_hi, st);
-    return project_bs<R, D, kBS64>(P, tab, first, S, partial, i_lo, i_hi, st);
+    constexpr size_t cap = 227 * 1024;
+    // room for at least 64 coefficients per pass besides the table and the power tables
+    auto fits = [&](int bs, bool tg) {
+        return tab_smem(P, tg) + (size_t)D * P.K1 * bs * sizeof(V2<R>) + (bs / 32) * 64 * sizeof(V2<R>) <= cap;
+    };
+    if (sizeof(R) == 4 && fits(kBS32, false)) return project_bs<R, D, kBS32, false>(P, tab, first, S, partial, i_lo, i_hi, st);
+    if (fits(kBS64, false)) return project_bs<R, D, kBS64, false>(P, tab, first, S, partial, i_lo, i_hi, st);
+    return project_bs<R, D, kBS64, true>(P, tab, first, S, partial, i_lo, i_hi, st);
 }
 
-template <typename R, int D>
-static cudaError_t eval_t(const QrParams& P, const GEntry* tab, const uint8_t* first, const void* row,
-                          const double* x, long long n, double* y, int use_g, cudaStream_t st)
+template <typename R, int D, bool TG>
+static cudaError_t eval_bs(const QrParams& P, const GEntry* tab, const uint8_t* first, const void* row,
+                           const double* x, long long n, double* y, int use_g, cudaStream_t st)
 {
     constexpr int BS = 128;
-    const size_t sm = align16((size_t)P.nGp * sizeof(GEntry)) + align16((size_t)P.nGp) +
-                      align16((size_t)P.nGp * sizeof(V2<R>)) + (size_t)D * P.K1 * BS * sizeof(V2<R>);
+    const size_t sm = tab_smem(P, TG) + align16((size_t)P.nGp * sizeof(V2<R>)) + (size_t)D * P.K1 * BS * sizeof(V2<R>);
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
-    auto kern = k_eval<R, D, BS>;
+    auto kern = k_eval<R, D, BS, TG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     if (n <= 0) return cudaSuccess;
     kern<<<(unsigned)((n + BS - 1) / BS), BS, sm, st>>>(P, tab, first, static_cast<const V2<R>*>(row), x, n, y,
                                                          use_g);
     return cudaGetLastError();
+}
+
+template <typename R, int D>
+static cudaError_t eval_t(const QrParams& P, const GEntry* tab, const uint8_t* first, const void* row,
+                          const double* x, long long n, double* y, int use_g, cudaStream_t st)
+{
+    const size_t rest = align16((size_t)P.nGp * sizeof(V2<R>)) + (size_t)D * P.K1 * 128 * sizeof(V2<R>);
+    if (tab_smem(P, false) + rest <= 227 * 1024) return eval_bs<R, D, false>(P, tab, first, row, x, n, y, use_g, st);
+    return eval_bs<R, D, true>(P, tab, first, row, x, n, y, use_g, st);
 }
 
 template <typename R, int D>

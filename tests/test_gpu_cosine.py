@@ -38,6 +38,7 @@ def _oracle_problem(ora, p: W.Sec5Problem, M=None):
     (2, W.G_HYP_N, 7, 5, 2500, (0, 1)),
     (3, W.G_TOTAL_N, 3, 4, 1500, (0, 1)),
     (6, W.G_TOTAL_N, 5, 4, 1100, (0, 1)),    # unfolds to |k|_1 <= 5: compile-time tree kernels
+    (3, W.G_TOTAL_N, 22, 2, 700, (1,)),      # 15225 unfolded entries: index table read from global memory
 ])
 def test_cosine_picard_matches_oracle(mods, ora, d, kind, n, N, M, precs):
     solver = mods
