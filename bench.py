@@ -300,7 +300,9 @@ def main():
                      "kernel": "k_paths (path-and-series)",
                      "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived; no FP32 peak in "
                                    "MEASURED_PEAKS.json)",
-                     "work": "M N(N-1)/2 series points x (|Gamma|+1)/2 pairs x 8 flop"},
+                     "work": "M N(N-1)/2 series points x (|Gamma|+1)/2 pairs x 8 flop",
+                     "peak_at_measured_clock": fp32_peak_tflops(clocks["sm_mhz"] or 2032.0),
+                     "frac_at_measured_clock": achieved / fp32_peak_tflops(clocks["sm_mhz"] or 2032.0)},
         "clocks": clocks,
         "gpu_launches": 4 * args.steps,  # per iteration: path, projection, reduction, tree repack
         "e2e": {"value": e2e_val, "unit": "path.coef evals/s", "h2d_bytes_per_step": io_bytes,
