@@ -11,7 +11,9 @@
  * represented by its coefficients alpha_{i,k}, k in an index set Gamma of
  * Z^d, on the nu-orthonormal basis phi_k(x) = prod_l e^{2 pi i k_l F_nu(x_l)}
  * (Sec. 2.2 with complex exponentials in place of cosines):
- *     ybar_i(x) = Re sum_{k in Gamma} alpha_{i,k} phi_k(x).
+ *     ybar_i(x) = Re sum_{k in Gamma} alpha_{i,k} phi_k(x),
+ * or on the paper's own cosine basis over an N^d set (index-set kinds 3-5
+ * below), optionally with the damping exponent q of eq. (yqi).
  * One Picard iteration recomputes every row i from the previous iterate at
  * once; each row is the Monte-Carlo projection of Algorithm 1 (Sec. 2.3):
  *     alpha_{i,k} = (1/M) sum_m S_i^m conj(phi_k(X_i^{i,m})),  X_i^{i,m} ~ nu,
