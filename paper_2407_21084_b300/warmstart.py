@@ -224,6 +224,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--test-points", type=int, default=1024)
     ap.add_argument("--target-scale", choices=("global", "per_output"), default="global")
+    ap.add_argument("--warm-kmax", type=int, nargs="*", default=[],
+                    help="also start from the prediction kept on |k|_1 <= each of these")
     args = ap.parse_args()
     import torch
 
@@ -247,11 +249,15 @@ def main():
             pts = [ref.test_points(i, args.test_points) for i in range(w.N)]
             y_ref = [ref.eval(i, x) for i, x in enumerate(pts)]
         res = {}
-        forms = (("fp64_cold", FP64, False), ("fp32_cold", FP32, False), ("fp32_warm", FP32, True))
-        for name, prec, warm in forms[0 if q < args.heldout_fp64 else 1:]:
+        pred = rows_to_alpha(net.predict(features(w)))
+        forms = [("fp64_cold", FP64, None), ("fp32_cold", FP32, None), ("fp32_warm", FP32, 10 ** 9)]
+        forms += [("fp32_warm_k%d" % kc, FP32, kc) for kc in args.warm_kmax]
+        for name, prec, kcut in forms[0 if q < args.heldout_fp64 else 1:]:
             with Solver.from_workload(w, precision=prec) as s:
-                if warm:
-                    s.set_coefs(rows_to_alpha(net.predict(features(w))))
+                if kcut is not None:
+                    # the network's start, optionally kept only on |k|_1 <= kcut
+                    keep = np.abs(s.gamma_list()).sum(axis=1) <= kcut
+                    s.set_coefs(np.where(keep[None, :], pred, 0.0))
                 it, secs, err = iterate_to(s, pts, y_ref, args.tol, w.N + 2)
                 res[name] = {"iterations": it, "seconds": secs, "sup_error": err}
         # Algorithm 1 itself (one backward sweep, rows in sequence) in FP32
@@ -263,10 +269,11 @@ def main():
             res["fp32_sweep"] = {"iterations": 1, "seconds": time.perf_counter() - t0,
                                  "sup_error": sup_error(s, pts, y_ref)}
         rows.append(res)
+    names = ["fp64_cold", "fp32_cold", "fp32_warm"] + ["fp32_warm_k%d" % kc for kc in args.warm_kmax] + ["fp32_sweep"]
     summ = {k: {"iterations_mean": float(np.mean([r[k]["iterations"] for r in rows if k in r])),
                 "seconds_mean": float(np.mean([r[k]["seconds"] for r in rows if k in r])),
                 "problems": sum(k in r for r in rows)}
-            for k in ("fp64_cold", "fp32_cold", "fp32_warm", "fp32_sweep")}
+            for k in names}
     print(json.dumps({"train_solves": args.train, "train_paths": args.train_paths, "target_scale": args.target_scale,
                       "data_s": t_data,
                       "fit_s": t_fit, "loss_first": hist[0], "loss_last": hist[-1], "heldout": args.heldout,
