@@ -55,3 +55,36 @@ def test_new_classes_match_oracle(mods, ora, d, n):
             s.picard_step(2)
             a = s.coefs()
         assert np.abs(a - ref).max() / np.abs(ref).max() < tol
+
+
+def test_c4_full_size_sampled_responses(mods, ora):
+    """The multi-instance workload at its full size (256 instances of uneven
+    d, |Gamma| and N, M = 2^18 each, 64 of them sharing their points and run
+    by the tensor-core path), in the launch geometry `batch.py` times: after
+    one batch iteration from y == 0, the responses of the second iteration
+    are checked path by path against the oracle, from the coefficients the
+    first one produced, on a sample of instances, rows and paths."""
+    batch, solver, torch = mods
+    ws = W.c4()
+    st = torch.cuda.Stream()
+    sol = batch.solvers_for(ws, st.cuda_stream)
+    b = batch.Batch(sol)
+    assert b.info()["grouped_instances"] == 64
+    b.picard_step(1)
+    rng = np.random.default_rng(44)
+    picks = sorted(set([0, 1] + list(rng.choice(len(ws) - 64, 3, replace=False)) + [len(ws) - 64, len(ws) - 1]))
+    a1 = {q: sol[q].coefs() for q in picks}
+    b.picard_step(1)
+    for q in picks:
+        w, s = ws[q], sol[q]
+        K = ora.gamma_list(w.gamma_kind, w.d, w.gamma_n)
+        p = ora.Problem(d=w.d, N=w.N, T=w.T, k=K, b=w.b, sigma=w.sigma, f_kind=ora.F_CUBIC_MANUF, f_par=w.f_par,
+                        g_kind=ora.GT_COS, g_par=w.g_par, M=w.M, seed=w.seed, clamp_L=w.clamp_L)
+        for i in (0, w.N // 2, w.N - 1):
+            S = s.responses(i)
+            for m in rng.integers(0, w.M, size=6):
+                So = ora.responses(p, a1[q], i, (int(m), int(m) + 1))[0]
+                assert abs(S[m] - So) < 1e-4 * max(1.0, abs(So)), (w.name, i, int(m))
+    b.close()
+    for s in sol:
+        s.close()
