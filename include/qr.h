@@ -228,7 +228,8 @@ qr_status qr_selftest_wait_timeout(qr_ctx* ctx);
  * d = 2; |k|_1 <= 5 (d = 3), 4 (d = 4, 5, 6), 3 (d = 6, 7, 8)) by Picard
  * iterations together. The path-and-series phase of all instances is one
  * persistent kernel launch pulling (instance, time index, path tiles) work
- * items longest-first; projection and reduction follow per instance; one
+ * items, class by class and longest first within a class; projection and
+ * reduction follow per instance; one
  * iteration is one CUDA graph launch. The first qr_batch_picard_step times a
  * few item sizes and grids and keeps the fastest (autotuning). The batch
  * does not own the contexts: destroy it before them. Results per instance

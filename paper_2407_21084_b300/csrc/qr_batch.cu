@@ -3,8 +3,10 @@
 //
 // The path-and-series phase of all instances is ONE persistent kernel: every
 // CTA takes work items (instance, time index i, run of path tiles) from a
-// global counter, items ordered longest first (work ~ N - i) so that the
-// long rows start early and the short ones fill the tail. Each item runs the
+// global counter. Items are ordered class by class (the class with the most
+// work first) and longest first (work ~ N - i) within a class, so that the
+// CTAs running at any time mostly execute the same body (shared instruction
+// caches) and the short rows fill each class's tail. Each item runs the
 // compile-time chain-tree body of its instance's index-set class (a switch
 // over the compiled classes; the class is uniform per item). Coefficient
 // rows are staged in a double buffer sized for the largest row; mbarrier
