@@ -78,7 +78,7 @@ typedef struct {
  * with the complex Fourier basis phi_k(x) = e^{2 pi i k.F_nu(x)}. Kinds 3-5
  * are the N^d sets of Sec. 2.4.2 with the paper's cosine basis
  * phi_k(x) = prod_l C_{k_l}(F_nu(x_l)), C_0 = 1, C_k = sqrt(2) cos(k pi u)
- * (Lemma ortho:dim1). A cosine context works on the unfolded set
+ * (Lemma ortho:dim1). Internally a cosine context works on the unfolded set
  * {m in Z^d : |m| in Gamma} (Gamma_F(n) -> kind 0, Gamma_T(n) -> kind 1,
  * Gamma_H(n) -> kind 2, same n) with half-angle phases e^{i pi m.F_nu(x)}:
  * a cosine series sum_k a_k phi_k equals Re sum_m c_m e^{i pi m.F_nu(x)} with
@@ -86,8 +86,9 @@ typedef struct {
  * and after every projection the coefficients are averaged over the sign
  * orbits, which is the cosine projection of eq. (Aqi:bar:M) in these
  * coordinates. qr_gamma_size/list, qr_get/set_coefs and a QR_GT_TRIGPOLY g
- * use the unfolded set and the coefficients c_m (a_k = 2^{d'(k)/2} c_k for
- * k in N^d). Canonical order: lexicographic, k_1 most significant. The
+ * use Gamma itself (the N^d set) and the cosine coefficients a_k: real
+ * values in the interleaved complex layout (imaginary parts 0 on output,
+ * ignored on input). Canonical order: lexicographic, k_1 most significant. The
  * generic kernels hold per-lane power tables of d (max|k_l| + 1) complex
  * values in shared memory; qr_init returns QR_ENOTIMPL when they exceed it. */
 enum {

@@ -50,6 +50,12 @@ struct qr_ctx {
     // with half-angle phases; raw projections are symmetrised over the sign
     // orbits (CSR over the canonical order) after every reduction
     bool cosine = false;
+    // the N^d set Gamma of a cosine context (canonical order) and its maps to
+    // the unfolded set: z_of_n[q] = unfolded index of k_q; n_of_z[e] = index
+    // in Gamma of |m_e|; zscale[e] = 2^{-d'(m_e)/2} (c_m = a_|m| zscale)
+    int nGn = 0;
+    std::vector<int> kn, z_of_n, n_of_z;
+    std::vector<double> zscale;
     double2* d_alpha_raw = nullptr;
     int* d_orb_off = nullptr;
     int* d_orb_idx = nullptr;
@@ -457,6 +463,33 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     // index set and coefficient table
     enumerate_gamma(zkind, d, gamma->n, c->k);
     c->cosine = cosine;
+    if (cosine) {
+        const int nz = (int)(c->k.size() / d);
+        std::map<std::vector<int>, int> nidx;
+        for (int e = 0; e < nz; ++e) {
+            std::vector<int> kv(c->k.begin() + (size_t)e * d, c->k.begin() + (size_t)(e + 1) * d);
+            bool nonneg = true;
+            for (int v : kv) nonneg = nonneg && v >= 0;
+            if (nonneg) {
+                nidx[kv] = (int)c->z_of_n.size();
+                c->z_of_n.push_back(e);
+                c->kn.insert(c->kn.end(), kv.begin(), kv.end());
+            }
+        }
+        c->nGn = (int)c->z_of_n.size();
+        c->n_of_z.resize(nz);
+        c->zscale.resize(nz);
+        for (int e = 0; e < nz; ++e) {
+            std::vector<int> kv(c->k.begin() + (size_t)e * d, c->k.begin() + (size_t)(e + 1) * d);
+            int dn = 0;
+            for (int& v : kv) {
+                dn += v != 0;
+                v = v < 0 ? -v : v;
+            }
+            c->n_of_z[e] = nidx.at(kv);
+            c->zscale[e] = std::pow(2.0, -0.5 * dn);
+        }
+    }
     c->nG = (int)(c->k.size() / d);
     c->zero_idx = (c->nG - 1) / 2;
     for (int l = 0; l < d; ++l)
@@ -552,7 +585,8 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
         P.g_kap = g->params[0];
         P.g_lam = g->params[1];
     } else if (g->kind == QR_GT_TRIGPOLY) {
-        if (!g->params || g->n_params < 2 * c->nG) return bail(QR_EINVAL, "polynomial terminal needs 2|Gamma| values");
+        if (!g->params || g->n_params < 2 * (cosine ? c->nGn : c->nG))
+            return bail(QR_EINVAL, "polynomial terminal needs 2|Gamma| values");
         c->trig_g = true;
     } else {
         return bail(QR_EINVAL, "unknown terminal condition");
@@ -604,8 +638,16 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
             QR_OK ||
         (s = cu(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream), "zero status")) != QR_OK)
         return bail(s, c->err);
+    std::vector<double2> g_unfolded;  // a cosine polynomial g on the unfolded set (lives until the final sync)
     if (c->trig_g) {
-        if ((s = cu(cudaMemcpyAsync(c->d_alpha + (size_t)N * c->nG, g->params, sizeof(double2) * c->nG,
+        const double2* src = reinterpret_cast<const double2*>(g->params);
+        if (cosine) {
+            g_unfolded.resize(c->nG);
+            for (int e = 0; e < c->nG; ++e)
+                g_unfolded[e] = make_double2(g->params[2 * c->n_of_z[e]] * c->zscale[e], 0.0);
+            src = g_unfolded.data();
+        }
+        if ((s = cu(cudaMemcpyAsync(c->d_alpha + (size_t)N * c->nG, src, sizeof(double2) * c->nG,
                                     cudaMemcpyHostToDevice, c->stream),
                     "copy terminal polynomial")) != QR_OK)
             return bail(s, c->err);
@@ -795,14 +837,15 @@ qr_status qr_eval(qr_ctx* ctx, int i, const double* x, long long n, double* y_ou
 qr_status qr_gamma_size(const qr_ctx* ctx, int* n_gamma)
 {
     if (!ready(ctx) || !n_gamma) return QR_EINVAL;
-    *n_gamma = ctx->nG;
+    *n_gamma = ctx->cosine ? ctx->nGn : ctx->nG;
     return QR_OK;
 }
 
 qr_status qr_gamma_list(const qr_ctx* ctx, int* k_out)
 {
     if (!ready(ctx) || !k_out) return QR_EINVAL;
-    std::memcpy(k_out, ctx->k.data(), sizeof(int) * ctx->k.size());
+    const std::vector<int>& k = ctx->cosine ? ctx->kn : ctx->k;
+    std::memcpy(k_out, k.data(), sizeof(int) * k.size());
     return QR_OK;
 }
 
@@ -810,18 +853,43 @@ qr_status qr_get_coefs(const qr_ctx* ctx, double* alpha_out)
 {
     if (!ready(ctx) || !alpha_out) return QR_EINVAL;
     qr_ctx* c = const_cast<qr_ctx*>(ctx);
-    QR_CU(c, cudaMemcpyAsync(alpha_out, ctx->d_alpha, sizeof(double2) * (size_t)ctx->N * ctx->nG, cudaMemcpyDeviceToHost,
-                             ctx->stream));
+    if (!ctx->cosine) {
+        QR_CU(c, cudaMemcpyAsync(alpha_out, ctx->d_alpha, sizeof(double2) * (size_t)ctx->N * ctx->nG,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        QR_CU(c, cudaStreamSynchronize(ctx->stream));
+        return QR_OK;
+    }
+    // cosine: a_k = c_k / zscale(k) from the unfolded rows
+    std::vector<double2> z((size_t)ctx->N * ctx->nG);
+    QR_CU(c, cudaMemcpyAsync(z.data(), ctx->d_alpha, sizeof(double2) * z.size(), cudaMemcpyDeviceToHost, ctx->stream));
     QR_CU(c, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < ctx->N; ++i)
+        for (int q = 0; q < ctx->nGn; ++q) {
+            const int e = ctx->z_of_n[q];
+            alpha_out[2 * ((size_t)i * ctx->nGn + q)] = z[(size_t)i * ctx->nG + e].x / ctx->zscale[e];
+            alpha_out[2 * ((size_t)i * ctx->nGn + q) + 1] = 0.0;
+        }
     return QR_OK;
 }
 
 qr_status qr_set_coefs(qr_ctx* ctx, const double* alpha_in)
 {
     if (!ready(ctx) || !alpha_in) return QR_EINVAL;
-    for (long long t = 0; t < 2ll * ctx->N * ctx->nG; ++t)
+    const int n_in = ctx->cosine ? ctx->nGn : ctx->nG;
+    for (long long t = 0; t < 2ll * ctx->N * n_in; ++t)
         if (!std::isfinite(alpha_in[t])) return fail(ctx, QR_EINVAL, "qr_set_coefs: non-finite coefficient");
-    QR_CU(ctx, cudaMemcpyAsync(ctx->d_alpha, alpha_in, sizeof(double2) * (size_t)ctx->N * ctx->nG,
+    std::vector<double2> z;
+    const void* src = alpha_in;
+    if (ctx->cosine) {
+        // unfold the cosine coefficients (real parts) onto the Z^d set
+        z.resize((size_t)ctx->N * ctx->nG);
+        for (int i = 0; i < ctx->N; ++i)
+            for (int e = 0; e < ctx->nG; ++e)
+                z[(size_t)i * ctx->nG + e] =
+                    make_double2(alpha_in[2 * ((size_t)i * ctx->nGn + ctx->n_of_z[e])] * ctx->zscale[e], 0.0);
+        src = z.data();
+    }
+    QR_CU(ctx, cudaMemcpyAsync(ctx->d_alpha, src, sizeof(double2) * (size_t)ctx->N * ctx->nG,
                                cudaMemcpyHostToDevice, ctx->stream));
     QR_CU(ctx, launch_pack(ctx->prec, ctx->P, ctx->d_alpha, ctx->nG, ctx->zero_idx, ctx->d_packed, ctx->row_stride,
                            ctx->N, ctx->stream));

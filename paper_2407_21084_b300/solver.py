@@ -80,14 +80,9 @@ class Solver:
                    damping_q=p.q)
 
     def cosine_coefs(self):
-        """For a context of the cosine basis (N^d set): the N^d multi-indices
-        (canonical order) and the cosine coefficients a_k of every row,
-        a_k = 2^{d'(k)/2} c_k from the unfolded coefficients c_m."""
-        k = self.gamma_list()
-        keep = np.all(k >= 0, axis=1)
-        c = self.coefs()[:, keep].real
-        dnz = np.count_nonzero(k[keep], axis=1)
-        return k[keep], c * np.sqrt(2.0) ** dnz
+        """For a context of the cosine basis (N^d set): the multi-indices of
+        Gamma (canonical order) and the real cosine coefficients a_k of every row."""
+        return self.gamma_list(), self.coefs().real
 
     # -------------------------------------------------------------- calls
     def picard_step(self, n_iter: int = 1) -> float:

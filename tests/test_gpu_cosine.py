@@ -70,8 +70,9 @@ def test_cosine_backward_sweep_matches_oracle(mods, ora):
 
 
 def test_cosine_planted_polynomial_on_lattice(mods, ora):
-    """sigma = 0, f = 0, g = a cosine polynomial given through its unfolded
-    coefficients: every row recovers it exactly on the midpoint lattice."""
+    """sigma = 0, f = 0, g = a cosine polynomial given by its cosine
+    coefficients on Gamma: every row recovers it exactly on the midpoint
+    lattice, and set/get of the coefficients round-trips."""
     solver = mods
     from paper_2407_21084_b300 import _lib as L
 
@@ -79,19 +80,19 @@ def test_cosine_planted_polynomial_on_lattice(mods, ora):
     rng = np.random.default_rng(4)
     Kn = ora.gamma_list(W.G_TOTAL_N, d, n)
     a = rng.normal(size=len(Kn))
-    Kz = ora.gamma_list(W.G_L1_Z, d, n)
-    where = {tuple(k): e for e, k in enumerate(Kn)}
-    cz = np.array([a[where[tuple(np.abs(m))]] * 2.0 ** (-np.count_nonzero(m) / 2) for m in Kz])
-    g = np.zeros((len(Kz), 2))
-    g[:, 0] = cz
+    g = np.zeros((len(Kn), 2))
+    g[:, 0] = a
     for prec, tol in ((0, 1e-12), (1, 1e-5)):
         with solver.Solver(d, 3, 1.0, L.QR_NU_STUDENT2, 2.0, L.QR_G_TOTAL_N, n, np.zeros(d), np.zeros((d, d)),
                            L.QR_F_ZERO, [0.0], L.QR_GT_TRIGPOLY, g.ravel(), lat ** d, 1, precision=prec,
                            lattice_n=lat) as s:
             s.picard_step(1)
             k, got = s.cosine_coefs()
-        assert np.array_equal(k, Kn)
-        assert np.abs(got - a[None, :]).max() < tol * np.abs(a).max()
+            assert np.array_equal(k, Kn)
+            assert np.abs(got - a[None, :]).max() < tol * np.abs(a).max()
+            b = rng.normal(size=(3, len(Kn))).astype(complex)
+            s.set_coefs(b)
+            assert np.allclose(s.coefs(), b.real, rtol=1e-15, atol=1e-15)
 
 
 def test_paper_d1_confidence_interval(mods):
