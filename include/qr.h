@@ -116,7 +116,8 @@ enum {
 enum {
     QR_GT_COS = 0,        /* g = cos(s.x)                           params: {s_1..s_d} */
     QR_GT_TRIGPOLY = 1,   /* g = Re sum_{k in Gamma} c_k phi_k(x)   params: 2|Gamma| doubles
-                             (re, im interleaved, canonical order, c_{-k} = conj(c_k)) */
+                             (re, im interleaved, canonical order, c_{-k} = conj(c_k);
+                             cosine contexts: the real cosine coefficients on Gamma) */
     QR_GT_PAPER_SIN = 2   /* Sec. 5: g = 1 + kappa + sin(lambda sum x)  params: {kappa, lambda} */
 };
 typedef struct {
@@ -156,7 +157,9 @@ typedef struct {
 /* Creates a context: validates the problem, enumerates Gamma, allocates the
  * device state and sets alpha = 0 (ybar == 0 start).
  *   d in [1, 8]; N in [1, 256]; T > 0; b: d doubles (host); sigma: d*d doubles,
- *   row-major (host), X_{j+1} = X_j + b dt + sigma sqrt(dt) Z; every |k_l| <= 7.
+ *   row-major (host), X_{j+1} = X_j + b dt + sigma sqrt(dt) Z; every |k_l| <= 32767
+ *   for d <= 4 and <= 127 above (QR_ENOTIMPL otherwise, or when the generic
+ *   kernels' per-lane power tables and coefficient rows exceed shared memory).
  *   opts may be NULL: M = 2^14, seed 1, QR_FP64, no truncation. */
 qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const qr_gamma* gamma,
                   const double* b, const double* sigma, const qr_fn* f, const qr_fn* g,
@@ -183,7 +186,9 @@ qr_status qr_gamma_list(const qr_ctx* ctx, int* k_out);
 
 /* alpha: N*|Gamma| complex as interleaved (re, im) doubles, row i = time index
  * i, canonical Gamma order (host). set_coefs expects conjugate symmetry
- * alpha_{-k} = conj(alpha_k) and reads only k = 0 and the half k > 0. */
+ * alpha_{-k} = conj(alpha_k) and reads only k = 0 and the half k > 0. For a
+ * cosine context (kinds 3-5) the values are the real cosine coefficients a_k
+ * on Gamma (imaginary parts 0 on output, ignored on input). */
 qr_status qr_get_coefs(const qr_ctx* ctx, double* alpha_out);
 qr_status qr_set_coefs(qr_ctx* ctx, const double* alpha_in);
 
