@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "qr_batch.h"
+#include "qr_cosine.h"
 #include "qr_group.h"
 #include "qr_fast.h"
 #include "qr_internal.h"
@@ -59,6 +60,13 @@ struct qr_ctx {
     double2* d_alpha_raw = nullptr;
     int* d_orb_off = nullptr;
     int* d_orb_idx = nullptr;
+    // or run on Gamma itself by the direct cosine kernels (qr_cosine.cu):
+    // real rows of cos_groups groups of 4 packed positions; d_cpos[e] =
+    // packed position of entry e (then k == kn, nG == nGn, zero_idx == 0)
+    bool cos_direct = false;
+    int cos_groups = 0;
+    CosGroup* d_cgroups = nullptr;
+    int* d_cpos = nullptr;
     // one Picard iteration captured as a CUDA graph (built on first use when
     // profiling is off and the stream can be captured)
     cudaGraphExec_t graph = nullptr;
@@ -91,11 +99,12 @@ qr_status cuda_fail(qr_ctx* c, cudaError_t e, const char* where)
     } while (0)
 
 // Gamma of Z^d in canonical (lexicographic) order.
-void enumerate_gamma(int kind, int d, int n, std::vector<int>& out)
+// nonneg: only k in N^d (the index sets of the cosine basis), same order.
+void enumerate_gamma(int kind, int d, int n, std::vector<int>& out, bool nonneg = false)
 {
     std::vector<int> k(d, 0);
     std::function<void(int, long long, long long)> rec = [&](int l, long long s, long long prod) {
-        for (int v = -n; v <= n; ++v) {
+        for (int v = nonneg ? 0 : -n; v <= n; ++v) {
             const long long a = v < 0 ? -v : v;
             long long s2 = s, p2 = prod;
             if (kind == QR_G_LINF) {
@@ -265,7 +274,8 @@ void release(qr_ctx* c)
     if (c->stream || c->own_stream) {
         void* ptrs[] = {c->d_tab,     c->d_first,   c->d_alpha,    c->d_packed,    c->d_S,
                         c->d_partial, c->d_counters, c->d_status,   c->d_tree,      c->d_tmap,
-                        c->d_perm,    c->d_alpha_raw, c->d_orb_off, c->d_orb_idx};
+                        c->d_perm,    c->d_alpha_raw, c->d_orb_off, c->d_orb_idx, c->d_cgroups,
+                        c->d_cpos};
         for (void* p : ptrs)
             if (p) cudaFreeAsync(p, c->stream);
         cudaStreamSynchronize(c->stream);
@@ -323,9 +333,37 @@ cudaError_t pack_tree_rows(qr_ctx* c, int r_lo, int r_hi)
 }
 
 // one projection of rows [i_lo, i_hi) from the current packed coefficients
+qr_status run_rows_cos(qr_ctx* c, int i_lo, int i_hi)
+{
+    double* partial = reinterpret_cast<double*>(c->d_partial);
+    {
+        Timer t(c, 0);
+        cudaError_t e = launch_paths_cos(c->prec, c->P, c->d_cgroups, c->cos_groups, c->d_packed, c->row_stride,
+                                         c->d_S, i_lo, i_hi, c->d_counters, c->d_status, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "path-and-series kernel (cosine)");
+    }
+    harvest(c, 0);
+    {
+        Timer t(c, 1);
+        cudaError_t e = launch_project_cos(c->prec, c->P, c->d_cgroups, c->cos_groups, c->d_S, partial,
+                                           c->row_stride, i_lo, i_hi, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "projection kernel (cosine)");
+    }
+    harvest(c, 1);
+    {
+        Timer t(c, 2);
+        cudaError_t e = launch_reduce_cos(c->prec, c->P, partial, c->d_cpos, c->d_alpha, c->d_packed, c->row_stride,
+                                          i_lo, i_hi, c->d_counters, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "reduction kernel (cosine)");
+    }
+    harvest(c, 2);
+    return QR_OK;
+}
+
 qr_status run_rows(qr_ctx* c, int i_lo, int i_hi)
 {
     QR_CU(c, cudaMemsetAsync(c->d_counters + CNT_RESID, 0, sizeof(unsigned long long), c->stream));
+    if (c->cos_direct) return run_rows_cos(c, i_lo, i_hi);
     {
         Timer t(c, 0);
         cudaError_t e = c->tree_slots
@@ -461,63 +499,143 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     c->prec = o.precision;
 
     // index set and coefficient table
-    enumerate_gamma(zkind, d, gamma->n, c->k);
     c->cosine = cosine;
+    if (o.path_kernel < 0 || o.path_kernel > 2) return bail(QR_EINVAL, "unknown path kernel");
+    if (o.path_kernel == 2 && !cosine) return bail(QR_EINVAL, "path_kernel 2 (direct cosine kernels) needs a cosine index set");
+    std::vector<GEntry> tab;
+    std::vector<uint8_t> first;
+    std::vector<CosGroup> cgroups;
+    std::vector<int> cpos;
     if (cosine) {
-        const int nz = (int)(c->k.size() / d);
-        std::map<std::vector<int>, int> nidx;
-        for (int e = 0; e < nz; ++e) {
-            std::vector<int> kv(c->k.begin() + (size_t)e * d, c->k.begin() + (size_t)(e + 1) * d);
-            bool nonneg = true;
-            for (int v : kv) nonneg = nonneg && v >= 0;
-            if (nonneg) {
-                nidx[kv] = (int)c->z_of_n.size();
-                c->z_of_n.push_back(e);
-                c->kn.insert(c->kn.end(), kv.begin(), kv.end());
-            }
-        }
-        c->nGn = (int)c->z_of_n.size();
-        c->n_of_z.resize(nz);
-        c->zscale.resize(nz);
-        for (int e = 0; e < nz; ++e) {
-            std::vector<int> kv(c->k.begin() + (size_t)e * d, c->k.begin() + (size_t)(e + 1) * d);
+        // the direct kernels on Gamma itself, or the unfolded Z^d set on the
+        // Fourier kernels: unfolded when asked for (path_kernel 1) or when a
+        // compile-time tree kernel covers the unfolded set and its tables fit
+        std::vector<int> kn;
+        enumerate_gamma(zkind, d, gamma->n, kn, true);
+        const int nn = (int)(kn.size() / d);
+        long long nz = 0;
+        int km = 0;
+        for (int q = 0; q < nn; ++q) {
             int dn = 0;
-            for (int& v : kv) {
-                dn += v != 0;
-                v = v < 0 ? -v : v;
+            for (int l = 0; l < d; ++l) {
+                dn += kn[(size_t)q * d + l] != 0;
+                km = std::max(km, kn[(size_t)q * d + l]);
             }
-            c->n_of_z[e] = nidx.at(kv);
-            c->zscale[e] = std::pow(2.0, -0.5 * dn);
+            nz += 1ll << dn;
+        }
+        const size_t v2 = o.precision == QR_FP32 ? sizeof(float2) : sizeof(double2);
+        const double need = (double)d * (km + 1) * 128 * v2 + 2.0 * (double)((nz + 1) / 2) * v2 + 256;
+        const bool unfold_ok = km <= gentry_kmax(d) && need <= 227.0 * 1024;
+        c->cos_direct = o.path_kernel == 2 ||
+                        (o.path_kernel == 0 && (!unfold_ok || zkind == QR_G_HYP || tree_slots(zkind, d, gamma->n) == 0));
+        if (c->cos_direct) {
+            c->k = std::move(kn);
+            c->kmax = km;
+        } else if (!unfold_ok) {
+            return bail(QR_ENOTIMPL, "the unfolded set of this cosine index set exceeds the shared memory of the "
+                                     "table kernels (path_kernel 2 runs it on the direct kernels)");
         }
     }
-    c->nG = (int)(c->k.size() / d);
-    c->zero_idx = (c->nG - 1) / 2;
-    for (int l = 0; l < d; ++l)
-        if (c->k[(size_t)c->zero_idx * d + l] != 0) return bail(QR_EINVAL, "index set is not symmetric");
-    for (int v : c->k) c->kmax = std::max(c->kmax, v < 0 ? -v : v);
-    if (c->kmax > gentry_kmax(d))
-        return bail(QR_ENOTIMPL, d <= 4 ? "|k_l| <= 32767 is required" : "|k_l| <= 127 is required for d > 4");
-    {
-        // the table kernels (generic path, projection, evaluation) keep the
-        // powers z_l^a, a <= max|k_l|, of every lane in shared memory
-        const size_t v2 = o.precision == QR_FP32 ? sizeof(float2) : sizeof(double2);
-        const size_t nGp = (size_t)(c->nG - (c->nG - 1) / 2);
-        // (the index table itself moves to global memory when it does not fit)
-        const size_t need = (size_t)d * (c->kmax + 1) * 128 * v2 + 2 * nGp * v2 + 256;
-        if (need > 227 * 1024)
-            return bail(QR_ENOTIMPL, "index set too large for the table kernels: " + std::to_string(need / 1024) +
-                                         " KB of shared memory per block (limit 227 KB)");
-    }
-    c->nGp = c->nG - c->zero_idx;
-    std::vector<GEntry> tab(c->nGp);
-    std::vector<uint8_t> first(c->nGp, 0);
-    for (int e = 0; e < c->nGp; ++e) {
-        std::memset(tab[e].k8, 0, sizeof(tab[e].k8));
-        for (int l = 0; l < d && l < kDMax; ++l) tab[e].set(d, l, c->k[(size_t)(c->zero_idx + e) * d + l]);
-        if (e > 0) {
-            int f0 = 0;
-            while (f0 < d && tab[e].get(d, f0) == tab[e - 1].get(d, f0)) ++f0;
-            first[e] = (uint8_t)f0;
+    if (c->cos_direct) {
+        // runs of Gamma (common k_1..k_{d-1}, k_d = 0, 1, ...) in groups of 4 packed positions
+        c->nG = (int)(c->k.size() / d);
+        c->nGn = c->nG;
+        c->kn = c->k;
+        c->zero_idx = 0;
+        c->nGp = c->nG;
+        if (d > 1 && c->kmax > kCosPrefixMax)
+            return bail(QR_ENOTIMPL, "direct cosine kernels: k_l <= 255 is required for d > 1");
+        if (c->kmax > 65532) return bail(QR_ENOTIMPL, "direct cosine kernels: k <= 65532 is required");
+        if (!cos_paths_smem_min(o.precision, d, cos_k1p(c->kmax)))
+            return bail(QR_ENOTIMPL, "direct cosine kernels: the per-lane tables of d (max k + 1) values exceed "
+                                     "the shared memory of a 64-thread block");
+        cpos.resize(c->nG);
+        std::vector<int> prev(d > 1 ? d - 1 : 1, -1);
+        for (int e = 0; e < c->nG;) {
+            const int* ke = &c->k[(size_t)e * d];
+            int len = 0;
+            while (e + len < c->nG && std::equal(ke, ke + d - 1, &c->k[(size_t)(e + len) * d])) {
+                if (c->k[(size_t)(e + len) * d + d - 1] != len)
+                    return bail(QR_ENOTIMPL, "direct cosine kernels: a run of Gamma does not start at k_d = 0");
+                cpos[e + len] = 4 * (int)cgroups.size() + len;
+                ++len;
+            }
+            int f = 0;
+            if (d > 1 && e > 0)
+                while (f < d - 1 && ke[f] == prev[f]) ++f;
+            uint32_t kz = 0, kw = 0;
+            for (int l = 0; l + 1 < d; ++l) {
+                (l < 4 ? kz : kw) |= (uint32_t)ke[l] << (8 * (l & 3));
+                prev[l] = ke[l];
+            }
+            for (int a0 = 0; a0 < len; a0 += 4)
+                cgroups.push_back(make_uint4((uint32_t)a0 | (uint32_t)(a0 == 0 ? f : d - 1) << 16, 0u, kz, kw));
+            e += len;
+        }
+        while (cgroups.size() % 8) {
+            uint4 q = cgroups.back();
+            q.x = (uint32_t)(d - 1) << 16;  // zero coefficients: same run, k_d = 0..3
+            cgroups.push_back(q);
+        }
+        c->cos_groups = (int)cgroups.size();
+    } else {
+        enumerate_gamma(zkind, d, gamma->n, c->k);
+        if (cosine) {
+            const int nz = (int)(c->k.size() / d);
+            std::map<std::vector<int>, int> nidx;
+            for (int e = 0; e < nz; ++e) {
+                std::vector<int> kv(c->k.begin() + (size_t)e * d, c->k.begin() + (size_t)(e + 1) * d);
+                bool nonneg = true;
+                for (int v : kv) nonneg = nonneg && v >= 0;
+                if (nonneg) {
+                    nidx[kv] = (int)c->z_of_n.size();
+                    c->z_of_n.push_back(e);
+                    c->kn.insert(c->kn.end(), kv.begin(), kv.end());
+                }
+            }
+            c->nGn = (int)c->z_of_n.size();
+            c->n_of_z.resize(nz);
+            c->zscale.resize(nz);
+            for (int e = 0; e < nz; ++e) {
+                std::vector<int> kv(c->k.begin() + (size_t)e * d, c->k.begin() + (size_t)(e + 1) * d);
+                int dn = 0;
+                for (int& v : kv) {
+                    dn += v != 0;
+                    v = v < 0 ? -v : v;
+                }
+                c->n_of_z[e] = nidx.at(kv);
+                c->zscale[e] = std::pow(2.0, -0.5 * dn);
+            }
+        }
+        c->nG = (int)(c->k.size() / d);
+        c->zero_idx = (c->nG - 1) / 2;
+        for (int l = 0; l < d; ++l)
+            if (c->k[(size_t)c->zero_idx * d + l] != 0) return bail(QR_EINVAL, "index set is not symmetric");
+        for (int v : c->k) c->kmax = std::max(c->kmax, v < 0 ? -v : v);
+        if (c->kmax > gentry_kmax(d))
+            return bail(QR_ENOTIMPL, d <= 4 ? "|k_l| <= 32767 is required" : "|k_l| <= 127 is required for d > 4");
+        {
+            // the table kernels (generic path, projection, evaluation) keep the
+            // powers z_l^a, a <= max|k_l|, of every lane in shared memory
+            const size_t v2 = o.precision == QR_FP32 ? sizeof(float2) : sizeof(double2);
+            const size_t nGp = (size_t)(c->nG - (c->nG - 1) / 2);
+            // (the index table itself moves to global memory when it does not fit)
+            const size_t need = (size_t)d * (c->kmax + 1) * 128 * v2 + 2 * nGp * v2 + 256;
+            if (need > 227 * 1024)
+                return bail(QR_ENOTIMPL, "index set too large for the table kernels: " + std::to_string(need / 1024) +
+                                             " KB of shared memory per block (limit 227 KB)");
+        }
+        c->nGp = c->nG - c->zero_idx;
+        tab.resize(c->nGp);
+        first.assign(c->nGp, 0);
+        for (int e = 0; e < c->nGp; ++e) {
+            std::memset(tab[e].k8, 0, sizeof(tab[e].k8));
+            for (int l = 0; l < d && l < kDMax; ++l) tab[e].set(d, l, c->k[(size_t)(c->zero_idx + e) * d + l]);
+            if (e > 0) {
+                int f0 = 0;
+                while (f0 < d && tab[e].get(d, f0) == tab[e - 1].get(d, f0)) ++f0;
+                first[e] = (uint8_t)f0;
+            }
         }
     }
 
@@ -528,7 +646,7 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     P.q_damp = o.damping_q;
     P.N = N;
     P.nGp = c->nGp;
-    P.K1 = c->kmax + 1;
+    P.K1 = c->cos_direct ? cos_k1p(c->kmax) : c->kmax + 1;
     P.M = o.M;
     P.nu_kind = nu->kind;
     P.mu = nu->kind == QR_NU_LOMAX ? nu->mu : (nu->kind == QR_NU_STUDENT2 ? 2.0 : 1.0);
@@ -609,17 +727,28 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
         QR_CU(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         c->own_stream = true;
     }
-    c->elem = c->prec == QR_FP32 ? sizeof(float2) : sizeof(double2);
-    c->row_stride = c->prec == QR_FP32 ? ((c->nGp + 1) & ~1) : c->nGp;  // rows of 16-byte multiples
+    if (c->cos_direct) {  // real rows: groups of 4 positions (16 or 32 bytes)
+        c->elem = c->prec == QR_FP32 ? sizeof(float) : sizeof(double);
+        c->row_stride = 4ll * c->cos_groups;
+    } else {
+        c->elem = c->prec == QR_FP32 ? sizeof(float2) : sizeof(double2);
+        c->row_stride = c->prec == QR_FP32 ? ((c->nGp + 1) & ~1) : c->nGp;  // rows of 16-byte multiples
+    }
     qr_status s;
-    if ((s = dalloc(c, &c->d_tab, sizeof(GEntry) * c->nGp)) != QR_OK) return bail(s, c->err);
-    if ((s = dalloc(c, &c->d_first, c->nGp)) != QR_OK) return bail(s, c->err);
+    if ((s = dalloc(c, &c->d_tab, sizeof(GEntry) * tab.size())) != QR_OK) return bail(s, c->err);
+    if ((s = dalloc(c, &c->d_first, first.size())) != QR_OK) return bail(s, c->err);
     if ((s = dalloc(c, &c->d_alpha, sizeof(double2) * (size_t)(N + 1) * c->nG)) != QR_OK) return bail(s, c->err);
     if ((s = dalloc(c, &c->d_packed, c->elem * (size_t)(N + 1) * c->row_stride)) != QR_OK) return bail(s, c->err);
     if ((s = dalloc(c, &c->d_S, (c->prec == QR_FP32 ? 4 : 8) * (size_t)N * (size_t)o.M)) != QR_OK)
         return bail(s, c->err);
-    if ((s = dalloc(c, &c->d_partial, sizeof(double2) * (size_t)N * P.n_chunks * c->nGp)) != QR_OK)
-        return bail(s, c->err);
+    const size_t partial_bytes = c->cos_direct ? sizeof(double) * (size_t)N * P.n_chunks * c->row_stride
+                                               : sizeof(double2) * (size_t)N * P.n_chunks * c->nGp;
+    if ((s = dalloc(c, &c->d_partial, partial_bytes)) != QR_OK) return bail(s, c->err);
+    if (c->cos_direct) {
+        if ((s = dalloc(c, &c->d_cgroups, sizeof(CosGroup) * cgroups.size())) != QR_OK ||
+            (s = dalloc(c, &c->d_cpos, sizeof(int) * cpos.size())) != QR_OK)
+            return bail(s, c->err);
+    }
     if ((s = dalloc(c, &c->d_counters, sizeof(unsigned long long) * CNT_N)) != QR_OK) return bail(s, c->err);
     if ((s = dalloc(c, &c->d_status, sizeof(unsigned))) != QR_OK) return bail(s, c->err);
     if (cudaMallocHost(&c->h_counters, sizeof(unsigned long long) * CNT_N) != cudaSuccess)
@@ -628,10 +757,21 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
         if (cudaEventCreate(&e) != cudaSuccess) return bail(QR_ECUDA, "event creation failed");
 
     auto cu = [&](cudaError_t e, const char* w) { return e == cudaSuccess ? QR_OK : cuda_fail(c, e, w); };
-    if ((s = cu(cudaMemcpyAsync(c->d_tab, tab.data(), sizeof(GEntry) * c->nGp, cudaMemcpyHostToDevice, c->stream),
-                "copy table")) != QR_OK ||
-        (s = cu(cudaMemcpyAsync(c->d_first, first.data(), c->nGp, cudaMemcpyHostToDevice, c->stream), "copy table")) !=
-            QR_OK ||
+    if ((!tab.empty() &&
+         (s = cu(cudaMemcpyAsync(c->d_tab, tab.data(), sizeof(GEntry) * tab.size(), cudaMemcpyHostToDevice, c->stream),
+                 "copy table")) != QR_OK) ||
+        (!first.empty() &&
+         (s = cu(cudaMemcpyAsync(c->d_first, first.data(), first.size(), cudaMemcpyHostToDevice, c->stream),
+                 "copy table")) != QR_OK) ||
+        (c->cos_direct &&
+         ((s = cu(cudaMemcpyAsync(c->d_cgroups, cgroups.data(), sizeof(CosGroup) * cgroups.size(),
+                                  cudaMemcpyHostToDevice, c->stream),
+                  "copy groups")) != QR_OK ||
+          (s = cu(cudaMemcpyAsync(c->d_cpos, cpos.data(), sizeof(int) * cpos.size(), cudaMemcpyHostToDevice,
+                                  c->stream),
+                  "copy positions")) != QR_OK ||
+          (s = cu(cudaMemsetAsync(c->d_packed, 0, c->elem * (size_t)(N + 1) * c->row_stride, c->stream),
+                  "zero packed rows")) != QR_OK)) ||
         (s = cu(cudaMemsetAsync(c->d_alpha, 0, sizeof(double2) * (size_t)(N + 1) * c->nG, c->stream), "zero alpha")) !=
             QR_OK ||
         (s = cu(cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * CNT_N, c->stream), "zero counters")) !=
@@ -641,7 +781,11 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     std::vector<double2> g_unfolded;  // a cosine polynomial g on the unfolded set (lives until the final sync)
     if (c->trig_g) {
         const double2* src = reinterpret_cast<const double2*>(g->params);
-        if (cosine) {
+        if (c->cos_direct) {
+            g_unfolded.resize(c->nG);
+            for (int e = 0; e < c->nG; ++e) g_unfolded[e] = make_double2(g->params[2 * e], 0.0);
+            src = g_unfolded.data();
+        } else if (cosine) {
             g_unfolded.resize(c->nG);
             for (int e = 0; e < c->nG; ++e)
                 g_unfolded[e] = make_double2(g->params[2 * c->n_of_z[e]] * c->zscale[e], 0.0);
@@ -652,12 +796,16 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
                     "copy terminal polynomial")) != QR_OK)
             return bail(s, c->err);
     }
-    if ((s = cu(launch_pack(c->prec, P, c->d_alpha, c->nG, c->zero_idx, c->d_packed, c->row_stride, N + 1, c->stream),
+    if ((s = cu(c->cos_direct
+                    ? launch_pack_cos(c->prec, c->d_alpha, c->nG, c->d_cpos, c->d_packed, c->row_stride, N + 1,
+                                      c->stream)
+                    : launch_pack(c->prec, P, c->d_alpha, c->nG, c->zero_idx, c->d_packed, c->row_stride, N + 1,
+                                  c->stream),
                 "pack")) != QR_OK)
         return bail(s, c->err);
     c->gkind = zkind;
     c->gn = gamma->n;
-    if (o.path_kernel == 0 && zkind != QR_G_HYP) c->tree_slots = tree_slots(zkind, d, gamma->n);
+    if (o.path_kernel == 0 && zkind != QR_G_HYP && !c->cos_direct) c->tree_slots = tree_slots(zkind, d, gamma->n);
     if (c->tree_slots) {
         std::vector<TreeMap> map;
         if (!build_tree_map(zkind, d, gamma->n, c->k, map) || (int)map.size() != c->tree_slots)
@@ -670,10 +818,9 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
                     "copy tree map")) != QR_OK ||
             (s = cu(pack_tree_rows(c, 0, N + 1), "pack tree")) != QR_OK)
             return bail(s, c->err);
-    } else if (o.path_kernel != 0 && o.path_kernel != 1) {
-        return bail(QR_EINVAL, "unknown path kernel");
     }
-    if (o.path_kernel == 0 && zkind != QR_G_HYP) c->proj_nodes = proj_tree_nodes(zkind, d, gamma->n);
+    if (o.path_kernel == 0 && zkind != QR_G_HYP && !c->cos_direct)
+        c->proj_nodes = proj_tree_nodes(zkind, d, gamma->n);
     if (c->proj_nodes) {
         std::vector<int> perm;
         if (!build_proj_perm(zkind, d, gamma->n, c->k, c->zero_idx, perm) || (int)perm.size() != c->proj_nodes)
@@ -684,7 +831,7 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
                     "copy projection order")) != QR_OK)
             return bail(s, c->err);
     }
-    if (cosine) {
+    if (cosine && !c->cos_direct) {
         std::map<std::vector<int>, int> where;
         for (int e = 0; e < c->nG; ++e) where[std::vector<int>(c->k.begin() + (size_t)e * d, c->k.begin() + (size_t)(e + 1) * d)] = e;
         std::vector<int> off(1, 0), idx;
@@ -821,7 +968,10 @@ qr_status qr_eval(qr_ctx* ctx, int i, const double* x, long long n, double* y_ou
     }
     const int use_g = (i == ctx->N && !ctx->trig_g) ? 1 : 0;
     const void* row = static_cast<const char*>(ctx->d_packed) + ctx->elem * (size_t)i * ctx->row_stride;
-    cudaError_t e = launch_eval(ctx->prec, ctx->P, ctx->d_tab, ctx->d_first, row, dx, n, dy, use_g, ctx->stream);
+    cudaError_t e = ctx->cos_direct
+                        ? launch_eval_cos(ctx->prec, ctx->P, ctx->d_cgroups, ctx->cos_groups, row, dx, n, dy, use_g,
+                                          ctx->stream)
+                        : launch_eval(ctx->prec, ctx->P, ctx->d_tab, ctx->d_first, row, dx, n, dy, use_g, ctx->stream);
     if (e != cudaSuccess) {
         if (tmp) cudaFreeAsync(tmp, ctx->stream);
         return cuda_fail(ctx, e, "evaluation kernel");
@@ -853,7 +1003,7 @@ qr_status qr_get_coefs(const qr_ctx* ctx, double* alpha_out)
 {
     if (!ready(ctx) || !alpha_out) return QR_EINVAL;
     qr_ctx* c = const_cast<qr_ctx*>(ctx);
-    if (!ctx->cosine) {
+    if (!ctx->cosine || ctx->cos_direct) {  // direct cosine rows hold (a_k, 0)
         QR_CU(c, cudaMemcpyAsync(alpha_out, ctx->d_alpha, sizeof(double2) * (size_t)ctx->N * ctx->nG,
                                  cudaMemcpyDeviceToHost, ctx->stream));
         QR_CU(c, cudaStreamSynchronize(ctx->stream));
@@ -880,7 +1030,11 @@ qr_status qr_set_coefs(qr_ctx* ctx, const double* alpha_in)
         if (!std::isfinite(alpha_in[t])) return fail(ctx, QR_EINVAL, "qr_set_coefs: non-finite coefficient");
     std::vector<double2> z;
     const void* src = alpha_in;
-    if (ctx->cosine) {
+    if (ctx->cos_direct) {
+        z.resize((size_t)ctx->N * ctx->nG);
+        for (size_t t = 0; t < z.size(); ++t) z[t] = make_double2(alpha_in[2 * t], 0.0);
+        src = z.data();
+    } else if (ctx->cosine) {
         // unfold the cosine coefficients (real parts) onto the Z^d set
         z.resize((size_t)ctx->N * ctx->nG);
         for (int i = 0; i < ctx->N; ++i)
@@ -891,8 +1045,12 @@ qr_status qr_set_coefs(qr_ctx* ctx, const double* alpha_in)
     }
     QR_CU(ctx, cudaMemcpyAsync(ctx->d_alpha, src, sizeof(double2) * (size_t)ctx->N * ctx->nG,
                                cudaMemcpyHostToDevice, ctx->stream));
-    QR_CU(ctx, launch_pack(ctx->prec, ctx->P, ctx->d_alpha, ctx->nG, ctx->zero_idx, ctx->d_packed, ctx->row_stride,
-                           ctx->N, ctx->stream));
+    if (ctx->cos_direct)
+        QR_CU(ctx, launch_pack_cos(ctx->prec, ctx->d_alpha, ctx->nG, ctx->d_cpos, ctx->d_packed, ctx->row_stride,
+                                   ctx->N, ctx->stream));
+    else
+        QR_CU(ctx, launch_pack(ctx->prec, ctx->P, ctx->d_alpha, ctx->nG, ctx->zero_idx, ctx->d_packed,
+                               ctx->row_stride, ctx->N, ctx->stream));
     if (ctx->tree_slots) QR_CU(ctx, pack_tree_rows(ctx, 0, ctx->N));
     QR_CU(ctx, cudaStreamSynchronize(ctx->stream));
     return QR_OK;

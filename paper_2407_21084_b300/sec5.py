@@ -4,12 +4,12 @@ Test problem: dX = dW, g = 1 + kappa + sin(lam sum x), f = min(1, [y - kappa
 - 1 - sin(lam sum x) e^{lam^2 d (t-T)/2}]^2), kappa = 0.6, lam = 1/sqrt(d),
 T = 1, Student nu (mu = 2), cosine basis on Gamma_F (d = 1), Gamma_T or
 Gamma_H, damping exponents q of eq. (yqi), one backward sweep (Algorithm 1) in FP32 as in
-the paper. For each timed row of the paper's tables that fits the generic
-kernels on one GPU, prints one JSON line with
+the paper. For each timed row of the paper's tables (d = 1, 2, 3, 5, 7; the
+d = 9 and 11 rows need d > 8), prints one JSON line with
 
 * the wall time of one backward sweep here (CUDA-synchronised) and the
   paper's GPU time with the hardware it names (one GTX TITAN Black, Kepler,
-  FP32, CUDA 7.5), and W = M |Gamma| N(N+1)/2 path.coef evaluations per
+  FP32, CUDA 7.5; four of them for the d = 5 and 7 rows), and W = M |Gamma| N(N+1)/2 path.coef evaluations per
   second for both;
 * MSE_max and MSE_av of eq. (mse) against the exact solution (1000 test
   points per time index; damped by (1 + |x|^2)^{q/2} for q > 0), averaged
@@ -48,6 +48,20 @@ ROWS = [
     ("d3 Tot DEG22", 3, W.G_TOTAL_N, 22, 2300, 0.05, 2 * 10 ** 5, 53.89, {0.0: (-2.164, -2.785), 5.1: (-5.699, -6.141)}, None),
     ("d3 Hyp DEG20", 3, W.G_HYP_N, 20, 411, 0.05, 2 * 10 ** 5, 8.37, {0.0: (-2.255, -3.191), 5.1: (-6.883, -7.662)}, None),
     ("d3 Hyp DEG22", 3, W.G_HYP_N, 22, 459, 0.02, 2 * 10 ** 6, 592.19, {0.0: (-2.249, -3.356), 5.1: (-7.778, -8.875)}, None),
+    # the d = 5 and d = 7 tables give the times of the paper's multi-GPU code (4 GPUs)
+    ("d5 Tot DEG20", 5, W.G_TOTAL_N, 20, 53130, 0.2, 2 * 10 ** 6, 874.36,
+     {0.0: (-1.906, -2.049), 5.1: (-6.537, -6.994)}, None, 4),
+    ("d5 Tot DEG21", 5, W.G_TOTAL_N, 21, 65780, 0.1, 2 * 10 ** 7, 19163.72,
+     {0.0: (-2.221, -3.356), 5.1: (-8.482, -9.103)}, None, 4),
+    ("d5 Hyp DEG16", 5, W.G_HYP_N, 16, 3042, 0.2, 2 * 10 ** 6, 49.27,
+     {0.0: (-2.353, -3.259), 5.1: (-7.312, -7.835)}, None, 4),
+    ("d5 Hyp DEG17", 5, W.G_HYP_N, 17, 3122, 0.1, 2 * 10 ** 7, 773.70,
+     {0.0: (-1.955, -3.278), 5.1: (-7.438, -8.125)}, None, 4),
+    ("d5 Hyp DEG36", 5, W.G_HYP_N, 36, 10503, 0.1, 2 * 10 ** 7, 2718.07,
+     {0.0: (-2.216, -3.494), 5.1: (-8.609, -9.407)}, None, 4),
+    ("d5 Hyp DEG66", 5, W.G_HYP_N, 66, 24893, 0.1, 2 * 10 ** 7, 6563.77,
+     {0.0: (-2.381, -3.603), 5.1: (-8.819, -9.703)}, None, 4),
+    ("d7 Hyp DEG36", 7, W.G_HYP_N, 36, 94460, 0.1, 2 * 10 ** 7, 33284.41, {5.1: (-8.879, -9.574)}, None, 4),
 ]
 
 
@@ -55,25 +69,26 @@ def _problem(d, kind, n, delta, M, seed, q=0.0):
     return W.Sec5Problem(d=d, N=int(round(1.0 / delta)), gamma_kind=kind, gamma_n=n, M=M, seed=seed, q=q)
 
 
-def run_row(row, runs: int, ci_runs: int, precision=L.QR_FP32):
+def run_row(row, runs: int, ci_runs: int, precision=L.QR_FP32, path_kernel=0):
     import torch
 
     from .solver import Solver
 
-    label, d, kind, n, ng, delta, M, gpu_s, paper_mse, ci = row
+    label, d, kind, n, ng, delta, M, gpu_s, paper_mse, ci = row[:10]
+    paper_gpus = row[10] if len(row) > 10 else 1
     times, mse = [], {}
     for q in paper_mse:
         per = []
         for r in range(runs):
             p = _problem(d, kind, n, delta, M, seed=1 + r, q=q)
-            with Solver.from_sec5(p, precision=precision) as s:
+            with Solver.from_sec5(p, precision=precision, path_kernel=path_kernel) as s:
                 k, _ = s.cosine_coefs()
                 assert len(k) == ng, (label, len(k), ng)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 s.backward_sweep()
                 torch.cuda.synchronize()
-                if q == 0.0:
+                if q == min(paper_mse):
                     times.append(time.perf_counter() - t0)
                 per.append(s.mse_indicators(lambda t, x: p.exact_u(t, x), n=1000))
         mse[str(q)] = {"mse_max": float(np.mean([m["mse_max"] for m in per])),
@@ -86,13 +101,13 @@ def run_row(row, runs: int, ci_runs: int, precision=L.QR_FP32):
            "deg": n, "n_gamma": ng, "N": N, "M": M, "precision": "fp32" if precision == L.QR_FP32 else "fp64",
            "s_per_sweep": t, "evals_per_s": work / t,
            "paper_gpu_s": gpu_s, "paper_gpu_evals_per_s": work / gpu_s, "speedup_vs_paper_gpu": gpu_s / t,
-           "paper_hardware": "1x GeForce GTX TITAN Black (Kepler GK110), FP32, CUDA 7.5",
-           "mse_by_q": mse, "runs": runs}
+           "paper_hardware": "%dx GeForce GTX TITAN Black (Kepler GK110), FP32, CUDA 7.5" % paper_gpus,
+           "path_kernel": path_kernel, "mse_by_q": mse, "runs": runs}
     if ci is not None and ci_runs > 0:
         vals = []
         for r in range(ci_runs):
             p = _problem(d, kind, n, delta, M, seed=1001 + r)
-            with Solver.from_sec5(p, precision=precision) as s:
+            with Solver.from_sec5(p, precision=precision, path_kernel=path_kernel) as s:
                 s.backward_sweep()
                 vals.append(float(s.eval(0, np.zeros((1, d)))[0]))
         v = np.array(vals)
@@ -105,17 +120,19 @@ def run_row(row, runs: int, ci_runs: int, precision=L.QR_FP32):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--rows", default="d1,d2,d3", help="comma-separated prefixes of the row labels")
+    ap.add_argument("--rows", default="d1,d2,d3,d5,d7", help="comma-separated prefixes of the row labels")
     ap.add_argument("--runs", type=int, default=3, help="independent runs per row for time and MSE")
     ap.add_argument("--ci-runs", type=int, default=50, help="runs for the d = 1 confidence intervals")
     ap.add_argument("--max-gpu-s", type=float, default=3000.0, help="skip rows the paper timed above this")
+    ap.add_argument("--path-kernel", type=int, default=0,
+                    help="0: automatic; 1: the unfolded set on the Fourier kernels; 2: the direct cosine kernels")
     args = ap.parse_args()
     want = [w.strip() for w in args.rows.split(",") if w.strip()]
     for row in ROWS:
         if not any(row[0].startswith(w) for w in want) or row[7] > args.max_gpu_s:
             continue
         try:
-            out = run_row(row, args.runs, args.ci_runs)
+            out = run_row(row, args.runs, args.ci_runs, path_kernel=args.path_kernel)
         except L.QrError as e:  # e.g. an unfolded set too large for the generic kernels' shared memory
             out = {"row": row[0], "skipped": str(e)}
         print(json.dumps(out), flush=True)

@@ -44,7 +44,7 @@ def test_sm103a_code_object(lib):
     assert b"sm_103a" in data or b"sm_103" in data
 
 
-def _init(lib, d=2, N=4, T=1.0, gamma=(1, 2), M=64, prec=0, fkind=0, gkind=0, nu=(0, 3.0), lattice=0):
+def _init(lib, d=2, N=4, T=1.0, gamma=(1, 2), M=64, prec=0, fkind=0, gkind=0, nu=(0, 3.0), lattice=0, kern=0):
     from paper_2407_21084_b300 import _lib as L
 
     b = np.zeros(max(d, 1))
@@ -55,7 +55,7 @@ def _init(lib, d=2, N=4, T=1.0, gamma=(1, 2), M=64, prec=0, fkind=0, gkind=0, nu
                      b.ctypes.data_as(C.POINTER(C.c_double)), sig.ctypes.data_as(C.POINTER(C.c_double)),
                      C.byref(L.QrFn(fkind, par.ctypes.data_as(C.POINTER(C.c_double)), 16)),
                      C.byref(L.QrFn(gkind, par.ctypes.data_as(C.POINTER(C.c_double)), 16)),
-                     C.byref(L.QrOpts(M, 1, prec, 0.0, None, 1 if lattice else 0, lattice, 0)))
+                     C.byref(L.QrOpts(M, 1, prec, 0.0, None, 1 if lattice else 0, lattice, 0, kern)))
     msg = lib.qr_last_error(ctx).decode() if ctx else ""
     lib.qr_destroy(ctx)
     return st, msg
@@ -66,7 +66,8 @@ def _init(lib, d=2, N=4, T=1.0, gamma=(1, 2), M=64, prec=0, fkind=0, gkind=0, nu
     (dict(T=-1.0), "T must"), (dict(M=0), "M must"), (dict(prec=7), "precision"),
     (dict(gamma=(6, 2)), "index set"), (dict(gamma=(5, 0)), "index set"), (dict(d=5, gamma=(2, 128)), "|k_l| <= 127"),
     (dict(d=1, gamma=(0, 40000)), "|k_l| <= 32767"),
-    (dict(d=1, gamma=(3, 120)), "too large for the table kernels"), (dict(nu=(0, -1.0)), "mu"),
+    (dict(d=1, gamma=(3, 120), kern=1), "unfolded set"), (dict(d=1, gamma=(3, 40000)), "direct cosine kernels"),
+    (dict(kern=2), "needs a cosine index set"), (dict(kern=5), "unknown path kernel"), (dict(nu=(0, -1.0)), "mu"),
     (dict(fkind=9), "driver"), (dict(gkind=9), "terminal"), (dict(lattice=3, M=10), "lattice"),
 ])
 def test_host_validation_rejects_before_any_device_work(lib, kw, frag):

@@ -1,9 +1,11 @@
 """GPU parity of the cosine basis (Sec. 2.2, Lemma ortho:dim1) on the N^d
 sets Gamma_F, Gamma_T, Gamma_H against the FP64 oracle, which evaluates the
-cosines directly (the CUDA path runs the unfolded Z^d set at half angles and
-averages the projections over sign orbits). Also the paper's d = 1 test
-problem of Sec. 5: 50 independent runs give a 99 % interval for u(0,0) that
-contains 1.6 and overlaps the paper's [1.578, 1.667]."""
+cosines directly. Both CUDA routes run every case: path_kernel 1, the
+unfolded Z^d set at half angles on the Fourier kernels with the projections
+averaged over sign orbits, and path_kernel 2, the direct real kernels on
+Gamma (per-lane cosine tables, runs over the last coordinate). Also the
+paper's d = 1 test problem of Sec. 5: 50 independent runs give a 99 %
+interval for u(0,0) that contains 1.6 and overlaps the paper's [1.578, 1.667]."""
 import numpy as np
 import pytest
 
@@ -31,36 +33,54 @@ def _oracle_problem(ora, p: W.Sec5Problem, M=None):
                        nu_kind=ora.NU_STUDENT2, mu=2.0, basis=ora.BASIS_COS)
 
 
-@pytest.mark.parametrize("d,kind,n,N,M,precs", [
-    (1, W.G_FULL_N, 100, 6, 3000, (0, 1)),   # generic table kernel, 101 cosines
-    (1, W.G_FULL_N, 150, 5, 2000, (1,)),     # |k| > 127: 16-bit table entries; FP64 tables exceed shared memory
-    (2, W.G_TOTAL_N, 6, 5, 2500, (0, 1)),
-    (2, W.G_HYP_N, 7, 5, 2500, (0, 1)),
-    (3, W.G_TOTAL_N, 3, 4, 1500, (0, 1)),
-    (6, W.G_TOTAL_N, 5, 4, 1100, (0, 1)),    # unfolds to |k|_1 <= 5: compile-time tree kernels
-    (3, W.G_TOTAL_N, 22, 2, 700, (1,)),      # 15225 unfolded entries: index table read from global memory
+def _run(solver, p, prec, kern):
+    """A solver on route `kern`, or None where the unfolded route refuses the
+    set (its tables exceed shared memory); the direct route must take it."""
+    from paper_2407_21084_b300 import _lib as L
+
+    try:
+        return solver.Solver.from_sec5(p, precision=prec, path_kernel=kern)
+    except L.QrError as e:
+        assert kern == 1 and e.status == L.QR_ENOTIMPL, e
+        return None
+
+
+@pytest.mark.parametrize("kern", [1, 2])
+@pytest.mark.parametrize("d,kind,n,N,M", [
+    (1, W.G_FULL_N, 100, 6, 3000),   # 101 cosines
+    (1, W.G_FULL_N, 150, 5, 2000),   # |k| > 127; the unfolded FP64 tables exceed shared memory
+    (2, W.G_TOTAL_N, 6, 5, 2500),
+    (2, W.G_HYP_N, 7, 5, 2500),
+    (3, W.G_TOTAL_N, 3, 4, 1500),
+    (6, W.G_TOTAL_N, 5, 4, 1100),
+    (3, W.G_TOTAL_N, 22, 2, 700),    # 15225 unfolded entries: index table read from global memory
 ])
-def test_cosine_picard_matches_oracle(mods, ora, d, kind, n, N, M, precs):
+def test_cosine_picard_matches_oracle(mods, ora, d, kind, n, N, M, kern):
     solver = mods
     p = W.Sec5Problem(d=d, N=N, gamma_kind=kind, gamma_n=n, M=M, seed=9)
     ref, _ = ora.picard(_oracle_problem(ora, p), 2)
     ref = ref.real
+    ran = 0
     for prec, tol in ((0, 1e-10), (1, 1e-4)):
-        if prec not in precs:
+        s = _run(solver, p, prec, kern)
+        if s is None:
             continue
-        with solver.Solver.from_sec5(p, precision=prec) as s:
+        with s:
             s.picard_step(2)
             k, a = s.cosine_coefs()
         assert np.array_equal(k, ora.gamma_list(kind, d, n))
         err = np.abs(a - ref).max() / np.abs(ref).max()
         assert err < tol, (prec, err)
+        ran += 1
+    assert ran >= 1
 
 
-def test_cosine_backward_sweep_matches_oracle(mods, ora):
+@pytest.mark.parametrize("kern", [0, 2])
+def test_cosine_backward_sweep_matches_oracle(mods, ora, kern):
     solver = mods
     p = W.sec5_d1(K=100, N=20, M=20000, seed=3)
     ref, _ = ora.backward_sweep(_oracle_problem(ora, p))
-    with solver.Solver.from_sec5(p, precision=0) as s:
+    with solver.Solver.from_sec5(p, precision=0, path_kernel=kern) as s:
         s.backward_sweep()
         _, a = s.cosine_coefs()
         y0 = float(s.eval(0, np.zeros((1, 1)))[0])
@@ -69,7 +89,8 @@ def test_cosine_backward_sweep_matches_oracle(mods, ora):
     assert abs(y0 - y0_ref) < 1e-10
 
 
-def test_cosine_planted_polynomial_on_lattice(mods, ora):
+@pytest.mark.parametrize("kern", [1, 2])
+def test_cosine_planted_polynomial_on_lattice(mods, ora, kern):
     """sigma = 0, f = 0, g = a cosine polynomial given by its cosine
     coefficients on Gamma: every row recovers it exactly on the midpoint
     lattice, and set/get of the coefficients round-trips."""
@@ -85,7 +106,7 @@ def test_cosine_planted_polynomial_on_lattice(mods, ora):
     for prec, tol in ((0, 1e-12), (1, 1e-5)):
         with solver.Solver(d, 3, 1.0, L.QR_NU_STUDENT2, 2.0, L.QR_G_TOTAL_N, n, np.zeros(d), np.zeros((d, d)),
                            L.QR_F_ZERO, [0.0], L.QR_GT_TRIGPOLY, g.ravel(), lat ** d, 1, precision=prec,
-                           lattice_n=lat) as s:
+                           lattice_n=lat, path_kernel=kern) as s:
             s.picard_step(1)
             k, got = s.cosine_coefs()
             assert np.array_equal(k, Kn)
@@ -112,13 +133,14 @@ def test_paper_d1_confidence_interval(mods):
     assert lo <= 1.667 and hi >= 1.578, (lo, hi)
 
 
+@pytest.mark.parametrize("kern", [0, 1, 2])
 @pytest.mark.parametrize("d,kind,n,N,M,q", [
     (1, W.G_FULL_N, 40, 5, 3000, 5.1),
     (2, W.G_TOTAL_N, 6, 4, 2500, 2.1),
     (2, W.G_HYP_N, 7, 4, 2500, 8.1),
-    (6, W.G_TOTAL_N, 5, 3, 1100, 5.1),   # compile-time tree kernels with the damping weights
+    (6, W.G_TOTAL_N, 5, 3, 1100, 5.1),   # path_kernel 0: compile-time tree kernels with the damping weights
 ])
-def test_damped_picard_matches_oracle(mods, ora, d, kind, n, N, M, q):
+def test_damped_picard_matches_oracle(mods, ora, d, kind, n, N, M, q, kern):
     """Damping exponent q of eq. (yqi) in the responses of eq. (Sqi:bar:M)."""
     solver = mods
     p = W.Sec5Problem(d=d, N=N, gamma_kind=kind, gamma_n=n, M=M, seed=13, q=q)
@@ -127,7 +149,7 @@ def test_damped_picard_matches_oracle(mods, ora, d, kind, n, N, M, q):
     ref, _ = ora.picard(op, 2)
     ref = ref.real
     for prec, tol in ((0, 1e-10), (1, 1e-4)):
-        with solver.Solver.from_sec5(p, precision=prec) as s:
+        with solver.Solver.from_sec5(p, precision=prec, path_kernel=kern) as s:
             s.picard_step(2)
             _, a = s.cosine_coefs()
         err = np.abs(a - ref).max() / np.abs(ref).max()
