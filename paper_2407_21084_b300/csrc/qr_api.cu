@@ -66,6 +66,7 @@ struct qr_ctx {
     bool cos_direct = false;
     int cos_groups = 0;
     CosGroup* d_cgroups = nullptr;
+    uint8_t* d_cflags = nullptr;  // one byte per group: run start, changed prefix coordinate
     int* d_cpos = nullptr;
     // one Picard iteration captured as a CUDA graph (built on first use when
     // profiling is off and the stream can be captured)
@@ -275,7 +276,7 @@ void release(qr_ctx* c)
         void* ptrs[] = {c->d_tab,     c->d_first,   c->d_alpha,    c->d_packed,    c->d_S,
                         c->d_partial, c->d_counters, c->d_status,   c->d_tree,      c->d_tmap,
                         c->d_perm,    c->d_alpha_raw, c->d_orb_off, c->d_orb_idx, c->d_cgroups,
-                        c->d_cpos};
+                        c->d_cflags,  c->d_cpos};
         for (void* p : ptrs)
             if (p) cudaFreeAsync(p, c->stream);
         cudaStreamSynchronize(c->stream);
@@ -338,14 +339,14 @@ qr_status run_rows_cos(qr_ctx* c, int i_lo, int i_hi)
     double* partial = reinterpret_cast<double*>(c->d_partial);
     {
         Timer t(c, 0);
-        cudaError_t e = launch_paths_cos(c->prec, c->P, c->d_cgroups, c->cos_groups, c->d_packed, c->row_stride,
+        cudaError_t e = launch_paths_cos(c->prec, c->P, c->d_cflags, c->cos_groups, c->d_packed, c->row_stride,
                                          c->d_S, i_lo, i_hi, c->d_counters, c->d_status, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "path-and-series kernel (cosine)");
     }
     harvest(c, 0);
     {
         Timer t(c, 1);
-        cudaError_t e = launch_project_cos(c->prec, c->P, c->d_cgroups, c->cos_groups, c->d_S, partial,
+        cudaError_t e = launch_project_cos(c->prec, c->P, c->d_cgroups, c->d_cflags, c->cos_groups, c->d_S, partial,
                                            c->row_stride, i_lo, i_hi, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "projection kernel (cosine)");
     }
@@ -505,6 +506,7 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     std::vector<GEntry> tab;
     std::vector<uint8_t> first;
     std::vector<CosGroup> cgroups;
+    std::vector<uint8_t> cflags;
     std::vector<int> cpos;
     if (cosine) {
         // the direct kernels on Gamma itself, or the unfolded Z^d set on the
@@ -546,9 +548,6 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
         if (d > 1 && c->kmax > kCosPrefixMax)
             return bail(QR_ENOTIMPL, "direct cosine kernels: k_l <= 255 is required for d > 1");
         if (c->kmax > 65532) return bail(QR_ENOTIMPL, "direct cosine kernels: k <= 65532 is required");
-        if (!cos_paths_smem_min(o.precision, d, cos_k1p(c->kmax)))
-            return bail(QR_ENOTIMPL, "direct cosine kernels: the per-lane tables of d (max k + 1) values exceed "
-                                     "the shared memory of a 64-thread block");
         cpos.resize(c->nG);
         std::vector<int> prev(d > 1 ? d - 1 : 1, -1);
         for (int e = 0; e < c->nG;) {
@@ -563,19 +562,29 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
             int f = 0;
             if (d > 1 && e > 0)
                 while (f < d - 1 && ke[f] == prev[f]) ++f;
+            // the kernels step the prefix: coordinate f one up, the later ones back to 0
+            bool step_ok = true;
+            for (int l = 0; l + 1 < d; ++l) {
+                const int want = e == 0 ? 0 : (l < f ? prev[l] : (l == f ? prev[l] + 1 : 0));
+                step_ok = step_ok && ke[l] == want;
+            }
+            if (!step_ok) return bail(QR_ENOTIMPL, "direct cosine kernels: Gamma is not downward closed");
             uint32_t kz = 0, kw = 0;
             for (int l = 0; l + 1 < d; ++l) {
                 (l < 4 ? kz : kw) |= (uint32_t)ke[l] << (8 * (l & 3));
                 prev[l] = ke[l];
             }
-            for (int a0 = 0; a0 < len; a0 += 4)
-                cgroups.push_back(make_uint4((uint32_t)a0 | (uint32_t)(a0 == 0 ? f : d - 1) << 16, 0u, kz, kw));
+            for (int a0 = 0; a0 < len; a0 += 4) {
+                cgroups.push_back(make_uint4((uint32_t)a0, 0u, kz, kw));
+                cflags.push_back((uint8_t)(a0 == 0 ? 0x80 | (e == 0 ? d - 1 : f) : d - 1));
+            }
             e += len;
         }
-        while (cgroups.size() % 8) {
+        while (cgroups.size() % 16) {  // runs of zero coefficients under the last prefix
             uint4 q = cgroups.back();
-            q.x = (uint32_t)(d - 1) << 16;  // zero coefficients: same run, k_d = 0..3
+            q.x = 0;
             cgroups.push_back(q);
+            cflags.push_back((uint8_t)(0x80 | (d - 1)));
         }
         c->cos_groups = (int)cgroups.size();
     } else {
@@ -646,7 +655,7 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     P.q_damp = o.damping_q;
     P.N = N;
     P.nGp = c->nGp;
-    P.K1 = c->cos_direct ? cos_k1p(c->kmax) : c->kmax + 1;
+    P.K1 = c->kmax + 1;
     P.M = o.M;
     P.nu_kind = nu->kind;
     P.mu = nu->kind == QR_NU_LOMAX ? nu->mu : (nu->kind == QR_NU_STUDENT2 ? 2.0 : 1.0);
@@ -746,6 +755,7 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     if ((s = dalloc(c, &c->d_partial, partial_bytes)) != QR_OK) return bail(s, c->err);
     if (c->cos_direct) {
         if ((s = dalloc(c, &c->d_cgroups, sizeof(CosGroup) * cgroups.size())) != QR_OK ||
+            (s = dalloc(c, &c->d_cflags, cflags.size())) != QR_OK ||
             (s = dalloc(c, &c->d_cpos, sizeof(int) * cpos.size())) != QR_OK)
             return bail(s, c->err);
     }
@@ -767,6 +777,8 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
          ((s = cu(cudaMemcpyAsync(c->d_cgroups, cgroups.data(), sizeof(CosGroup) * cgroups.size(),
                                   cudaMemcpyHostToDevice, c->stream),
                   "copy groups")) != QR_OK ||
+          (s = cu(cudaMemcpyAsync(c->d_cflags, cflags.data(), cflags.size(), cudaMemcpyHostToDevice, c->stream),
+                  "copy run flags")) != QR_OK ||
           (s = cu(cudaMemcpyAsync(c->d_cpos, cpos.data(), sizeof(int) * cpos.size(), cudaMemcpyHostToDevice,
                                   c->stream),
                   "copy positions")) != QR_OK ||
@@ -969,7 +981,7 @@ qr_status qr_eval(qr_ctx* ctx, int i, const double* x, long long n, double* y_ou
     const int use_g = (i == ctx->N && !ctx->trig_g) ? 1 : 0;
     const void* row = static_cast<const char*>(ctx->d_packed) + ctx->elem * (size_t)i * ctx->row_stride;
     cudaError_t e = ctx->cos_direct
-                        ? launch_eval_cos(ctx->prec, ctx->P, ctx->d_cgroups, ctx->cos_groups, row, dx, n, dy, use_g,
+                        ? launch_eval_cos(ctx->prec, ctx->P, ctx->d_cflags, ctx->cos_groups, row, dx, n, dy, use_g,
                                           ctx->stream)
                         : launch_eval(ctx->prec, ctx->P, ctx->d_tab, ctx->d_first, row, dx, n, dy, use_g, ctx->stream);
     if (e != cudaSuccess) {

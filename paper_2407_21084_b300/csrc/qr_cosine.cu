@@ -1,20 +1,20 @@
 // qr_cosine.cu -- direct kernels of the cosine basis (Sec. 2.2, Lemma
 // ortho:dim1) on an N^d index set.
 //
-// phi_k(x) = prod_l C_{k_l}(F_nu(x_l)), C_0 = 1, C_a(u) = sqrt(2) cos(a pi u).
-// Every lane keeps the real table C_a(u_l), a < K1p, of its point in shared
-// memory (a column per lane, from the powers of z_l = e^{i pi u_l}, whose real
-// parts are cos(a pi u_l)). Along the runs of Gamma (entries sharing
-// k_1..k_{d-1}, with k_d = 0, 1, ...) the basis value is the run's prefix
-// product times C_{k_d}(u_d), so
-//   series      ybar(x) = sum_runs prefix(x) * sum_a c_{run,a} C_a(u_d)
-//               (one FMA and one table read per coefficient, a prefix
-//               product per run),
+// phi_k(x) = prod_l C_{k_l}(F_nu(x_l)), C_0 = 1, C_a(u) = sqrt(2) cos(a pi u)
+// = sqrt(2) Re z^a with z = e^{i pi u}. Along the runs of Gamma (entries
+// sharing k_1..k_{d-1}, with k_d = 0, 1, ...) the basis value is the run's
+// prefix product times C_{k_d}(u_d), and every factor is reached from the
+// previous one by one complex product (see CosWalk), so
+//   series      ybar(x) = sum_runs prefix(x) * sum_a c_{run,a} C_a(u_d):
+//               per coefficient one FMA and Re(P z^j) (two FMAs), per group of
+//               four one complex product, per run a prefix update;
 //   projection  a_k = (1/M) sum_m S^m phi_k(U^m), eq. (Aqi:bar:M), in tiles
 //               of 32 packed positions whose lane values are reduced over the
 //               warp by a 31-shuffle reduce-scatter.
-// Coefficient rows are real (half the bytes of the complex Fourier rows) and
-// Gamma is used as it is (no sign unfolding: 2^{d'} fewer entries). Responses
+// Everything per lane lives in registers (no per-lane tables), coefficient
+// rows are real (half the bytes of the complex Fourier rows) and Gamma is
+// used as it is (no sign unfolding: 2^{d'} fewer entries). Responses
 // (damping, truncation, driver, compensated sums), the bulk-copy staging of
 // the next row and the bounded waits follow the generic path kernel.
 #include "qr_cosine.h"
@@ -23,6 +23,8 @@
 #include <algorithm>
 
 namespace qr {
+
+constexpr int kCosBS = 128;
 
 namespace {
 
@@ -50,73 +52,167 @@ __device__ __forceinline__ void ld4<double>(const double* p, double& a, double& 
     d = v.y;
 }
 
-// C_a(u_l), a < K1p, into the lane's column t (stride BS) from z_l = e^{i pi u_l}
-template <typename R, int D, int BS>
-__device__ __forceinline__ void fill_cos(R* t, int K1p, const V2<R> (&z)[D])
-{
-    const R r2 = (R)1.4142135623730951;
+// Walk of one lane along Gamma in canonical order. For downward-closed sets
+// listed lexicographically, the prefix of a new run differs from the previous
+// one in one coordinate f, which grows by one, while the prefix coordinates
+// after f go back to 0 (checked on the host). So every factor is a power of
+// z_l = e^{i pi u_l} reached by one complex product from the previous one:
+// C_k(u_l) = sqrt(2) Re z_l^k (k >= 1), C_0 = 1; no tables.
+template <typename R, int D>
+struct CosWalk {
+    static constexpr int DP = D > 1 ? D - 1 : 1;
+    V2<R> z[D];        // e^{i pi u_l}
+    V2<R> w[DP];       // sqrt(2) z_l^{k_l} of the current prefix
+    R b[DP];           // b0 prod_{l' <= l} C_{k_l'}(u_l')
+    V2<R> z2, z3, z4;  // powers of the last coordinate's phase
+    V2<R> P;           // sqrt(2) z_d^a for the next group of the current run
+    R p;               // the current run's factor b0 prod_prefix C
+
+    // the walk before the first run (all prefix coordinates 0)
+    __device__ __forceinline__ void init(const V2<R> (&ph)[D], R b0)
+    {
 #pragma unroll
-    for (int l = 0; l < D; ++l) {
-        R* tl = t + (size_t)l * K1p * BS;
-        V2<R> p = z[l];
-        tl[0] = (R)1;
-        for (int a = 1; a < K1p; ++a) {
-            tl[(size_t)a * BS] = r2 * p.x;
-            p = cmul<R>(p, z[l]);
+        for (int l = 0; l < D; ++l) z[l] = ph[l];
+        const V2<R> zl = z[D - 1];
+        z2 = cmul<R>(zl, zl);
+        z3 = cmul<R>(z2, zl);
+        z4 = cmul<R>(z2, z2);
+#pragma unroll
+        for (int l = 0; l < DP; ++l) {
+            b[l] = b0;
+            w[l] = mk2<R>((R)1.4142135623730951, (R)0);
+        }
+        P = z4;
+        p = b0;
+    }
+
+    // prefix coordinate L one up, the later prefix coordinates back to 0
+    template <int L>
+    __device__ __forceinline__ void step(R b0)
+    {
+        w[L] = cmul<R>(w[L], z[L]);
+        b[L] = (L == 0 ? b0 : b[L == 0 ? 0 : L - 1]) * w[L].x;
+#pragma unroll
+        for (int l = L + 1; l < D - 1; ++l) {
+            w[l] = mk2<R>((R)1.4142135623730951, (R)0);
+            b[l] = b[L];
+        }
+        p = b[D - 2];
+    }
+
+    __device__ __forceinline__ void new_run(int f, R b0)
+    {
+        if constexpr (D > 1) {
+            if (f == D - 2) {  // the common case: the last prefix coordinate
+                step<D - 2>(b0);
+            } else {
+                step_at<0>(f, b0);
+            }
         }
     }
-}
+    template <int L>
+    __device__ __forceinline__ void step_at(int f, R b0)
+    {
+        if constexpr (L < D - 2) {
+            if (f == L)
+                step<L>(b0);
+            else
+                step_at<L + 1>(f, b0);
+        }
+    }
 
-// b[l] = b0 prod_{l' <= l} C_{k_l'}(u_l') for the prefix dimensions l = f .. d-2
-// (the lower ones are unchanged); returns b[d-2] (b0 when d = 1)
-template <typename R, int D, int BS>
-__device__ __forceinline__ R prefix_update(R (&b)[D], R b0, int f, uint32_t kz, uint32_t kw, const R* t, int K1p)
-{
-    if constexpr (D == 1) {
-        return b0;
-    } else {
-        if (f == D - 2) {  // the common case: only the last prefix coordinate changed
-            constexpr int l = D - 2;
-            const int kl = (int)(((l < 4 ? kz : kw) >> (8 * (l & 3))) & 0xffu);
-            b[l] = (l == 0 ? b0 : b[l == 0 ? 0 : l - 1]) * t[((size_t)l * K1p + kl) * BS];
+    // prefix k_1..k_{d-1} from scratch (bytes of kz, kw) and the last
+    // coordinate at a0: the state before the group that starts at a0
+    __device__ __forceinline__ void seek(uint32_t kz, uint32_t kw, int a0, R b0)
+    {
+        const R r2 = (R)1.4142135623730951;
+        if constexpr (D > 1) {
+#pragma unroll
+            for (int l = 0; l < D - 1; ++l) {
+                const int k = (int)(((l < 4 ? kz : kw) >> (8 * (l & 3))) & 0xffu);
+                V2<R> v = mk2<R>(r2, (R)0);
+                for (int t = 0; t < k; ++t) v = cmul<R>(v, z[l]);
+                w[l] = v;
+                const R below = l == 0 ? b0 : b[l == 0 ? 0 : l - 1];
+                b[l] = k == 0 ? below : below * v.x;
+            }
+            p = b[D - 2];
         } else {
-#pragma unroll
-            for (int l = 0; l < D - 1; ++l)
-                if (l >= f) {
-                    const int kl = (int)(((l < 4 ? kz : kw) >> (8 * (l & 3))) & 0xffu);
-                    b[l] = (l == 0 ? b0 : b[l == 0 ? 0 : l - 1]) * t[((size_t)l * K1p + kl) * BS];
-                }
+            p = b0;
         }
-        return b[D - 2];
+        if (a0 > 0) {
+            V2<R> v = mk2<R>(r2, (R)0);
+            for (int t = 0; t < a0; ++t) v = cmul<R>(v, z[D - 1]);
+            P = v;
+        }
     }
+
+    // C_{a+j}(u_d), j < 4, of the current run's next group (a = 0 when
+    // start); P moves on to a + 4
+    __device__ __forceinline__ void values(bool start, R& v0, R& v1, R& v2, R& v3)
+    {
+        const R r2 = (R)1.4142135623730951;
+        const V2<R> zl = z[D - 1];
+        if (start) {
+            v0 = (R)1;
+            v1 = r2 * zl.x;
+            v2 = r2 * z2.x;
+            v3 = r2 * z3.x;
+            P = mk2<R>(r2 * z4.x, r2 * z4.y);
+        } else {
+            v0 = P.x;
+            v1 = fma(P.x, zl.x, -P.y * zl.y);
+            v2 = fma(P.x, z2.x, -P.y * z2.y);
+            v3 = fma(P.x, z3.x, -P.y * z3.y);
+            P = cmul<R>(P, z4);
+        }
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ uint32_t word_of(const uint4& v, int h)
+{
+    return h == 0 ? v.x : (h == 1 ? v.y : (h == 2 ? v.z : v.w));
 }
 
-// sum_k c_k phi_k at the lane's point; c: packed real row (groups of 4)
-template <typename R, int D, int BS>
-__device__ __forceinline__ R cos_series(const R* __restrict__ c, const CosGroup* __restrict__ G, int ng, const R* t,
-                                        int K1p)
+// sum_k c_k phi_k at the walk's point; c: packed real row (groups of 4),
+// flags: one byte per group (bit 7: a run starts, bits 0-2: its first
+// changed prefix coordinate, d-1 for none), ng a multiple of 16
+template <typename R, int D>
+__device__ __forceinline__ R cos_series(const R* __restrict__ c, const uint4* __restrict__ flags, int ng,
+                                        CosWalk<R, D>& W)
 {
-    R b[D];
-    R p = (R)1, acc = (R)0, s0 = (R)0, s1 = (R)0;
-    const R* tl = t + (size_t)(D - 1) * K1p * BS;
-    for (int g = 0; g < ng; ++g) {
-        const uint4 q = __ldg(G + g);
-        const int a0 = (int)(q.x & 0xffffu), f = (int)(q.x >> 16);
-        if (D > 1 && f < D - 1) {  // a new run: close the previous one, new prefix product
-            acc = fma(p, s0 + s1, acc);
-            s0 = (R)0;
-            s1 = (R)0;
-            p = prefix_update<R, D, BS>(b, (R)1, f, q.z, q.w, t, K1p);
+    R acc = (R)0, s0 = (R)0, s1 = (R)0;
+    for (int g0 = 0; g0 < ng; g0 += 16) {
+        const uint4 fl = __ldg(flags + g0 / 16);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            // the coefficients of four groups first, then their values
+            R cc[16];
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                ld4<R>(c + 4 * (size_t)(g0 + 4 * h + t), cc[4 * t], cc[4 * t + 1], cc[4 * t + 2], cc[4 * t + 3]);
+            const uint32_t fw = word_of<R>(fl, h);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const uint32_t fb = (fw >> (8 * t)) & 0xffu;
+                const bool start = (fb & 0x80u) != 0;
+                if (start) {  // close the previous run
+                    acc = fma(W.p, s0 + s1, acc);
+                    s0 = (R)0;
+                    s1 = (R)0;
+                    if (D > 1 && (int)(fb & 7u) < D - 1) W.new_run((int)(fb & 7u), (R)1);
+                }
+                R v0, v1, v2, v3;
+                W.values(start, v0, v1, v2, v3);
+                s0 = fma(cc[4 * t], v0, s0);
+                s1 = fma(cc[4 * t + 1], v1, s1);
+                s0 = fma(cc[4 * t + 2], v2, s0);
+                s1 = fma(cc[4 * t + 3], v3, s1);
+            }
         }
-        R c0, c1, c2, c3;
-        ld4<R>(c + 4 * (size_t)g, c0, c1, c2, c3);
-        const R* ta = tl + (size_t)a0 * BS;
-        s0 = fma(c0, ta[0], s0);
-        s1 = fma(c1, ta[BS], s1);
-        s0 = fma(c2, ta[2 * BS], s0);
-        s1 = fma(c3, ta[3 * BS], s1);
     }
-    return fma(p, s0 + s1, acc);
+    return fma(W.p, s0 + s1, acc);
 }
 
 // reduce-scatter of 32 values over the warp: lane L returns the lane sum of v[L]
@@ -136,39 +232,33 @@ __device__ __forceinline__ R cos_fold32(R (&v)[32], int lane)
     return v[0];
 }
 
+// path kernel: two coefficient rows and two barriers (none when CG)
 template <typename R>
-__host__ __device__ size_t cos_table_bytes(int d, int K1p, int BS)
+size_t cos_paths_smem(long long row_stride, bool cg)
 {
-    return al16((size_t)d * K1p * BS * sizeof(R));
-}
-
-// path kernel: tables, then (CG = false) two coefficient rows and two barriers
-template <typename R>
-size_t cos_paths_smem(int d, int K1p, long long row_stride, int BS, bool cg)
-{
-    return cos_table_bytes<R>(d, K1p, BS) + (cg ? 0 : 2 * al16((size_t)row_stride * sizeof(R)) + 16);
+    return cg ? 0 : 2 * al16((size_t)row_stride * sizeof(R)) + 16;
 }
 
 }  // namespace
 
 // ------------------------------------------------------ path-and-series kernel
 // CG: the coefficient rows are read from global memory (L1/L2-resident,
-// warp-uniform) when two of them do not fit beside the tables
-template <typename R, int D, int BS, bool CG>
-__global__ void __launch_bounds__(BS) k_paths_cos(const __grid_constant__ QrParams P,
-                                                  const CosGroup* __restrict__ G, int ng,
-                                                  const R* __restrict__ packed, long long row_stride,
-                                                  R* __restrict__ S, int i_lo, int tiles_per_i,
-                                                  unsigned long long* __restrict__ counters,
-                                                  unsigned* __restrict__ status)
+// warp-uniform loads) instead of being staged in shared memory, for rows too
+// long to keep several blocks per SM
+template <typename R, int D, bool CG>
+__global__ void __launch_bounds__(kCosBS, sizeof(R) == 4 ? 4 : 2) k_paths_cos(const __grid_constant__ QrParams P,
+                                                         const uint4* __restrict__ flags, int ng,
+                                                         const R* __restrict__ packed, long long row_stride,
+                                                         R* __restrict__ S, int i_lo, int tiles_per_i,
+                                                         unsigned long long* __restrict__ counters,
+                                                         unsigned* __restrict__ status)
 {
+    constexpr int BS = kCosBS;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int K1p = P.K1, N = P.N;
-    const size_t tb = cos_table_bytes<R>(D, K1p, BS);
+    const int N = P.N;
     const uint32_t rowbytes = (uint32_t)al16((size_t)row_stride * sizeof(R));
-    R* tab = reinterpret_cast<R*>(smem);
-    R* abuf[2] = {reinterpret_cast<R*>(smem + tb), reinterpret_cast<R*>(smem + tb + rowbytes)};
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + tb + 2 * (size_t)rowbytes);
+    R* abuf[2] = {reinterpret_cast<R*>(smem), reinterpret_cast<R*>(smem + rowbytes)};
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * (size_t)rowbytes);
 
     const int tid = threadIdx.x;
     const int i = i_lo + (int)(blockIdx.x / tiles_per_i);
@@ -201,7 +291,6 @@ __global__ void __launch_bounds__(BS) k_paths_cos(const __grid_constant__ QrPara
     const R lw0 = damp ? damp_logw<R, D>(qh, x) : (R)0;  // log w(X_i^i)
     R sum = 0, comp = 0, gN = 0;
     unsigned long long hits = 0;
-    R* mytab = tab + tid;
     const R dt = (R)P.dt;
 
     for (int j = i; j < N; ++j) {
@@ -240,8 +329,9 @@ __global__ void __launch_bounds__(BS) k_paths_cos(const __grid_constant__ QrPara
             V2<R> zz[D];
 #pragma unroll
             for (int l = 0; l < D; ++l) zz[l] = nu_phase<R>(P, x1[l]);  // e^{i pi F(x)} (half angle)
-            fill_cos<R, D, BS>(mytab, K1p, zz);
-            y = cos_series<R, D, BS>(crow, G, ng, mytab, K1p);
+            CosWalk<R, D> W;
+            W.init(zz, (R)1);
+            y = cos_series<R, D>(crow, flags, ng, W);
             if (damp && row < N) y = undamp<R>(y, damp_logw<R, D>(qh, x1));  // y = ybar^q w(X_{j+1})
             if (row < N && P.clamp_L > 0.0) {
                 const R L = (R)P.clamp_L;
@@ -286,35 +376,34 @@ __global__ void __launch_bounds__(BS) k_paths_cos(const __grid_constant__ QrPara
 
 // --------------------------------------------------------- projection kernel
 // One CTA: row i, a chunk of P.chunk paths, a pass of KT packed positions
-// (a multiple of 32). Per round of BS paths every lane builds its table and
-// walks the pass with the prefix chain started at S^m, so that the chain's
-// last value is S^m phi_k(U^m); per tile of 32 positions the lane values are
-// reduce-scattered over the warp and added to the warp's accumulators in
-// shared memory, which are summed in fixed warp order at the end.
-template <typename R, int D, int BS>
-__global__ void __launch_bounds__(BS) k_project_cos(const __grid_constant__ QrParams P,
-                                                    const CosGroup* __restrict__ G, int ngroups,
-                                                    const R* __restrict__ S, double* __restrict__ partial,
-                                                    long long row_stride, int i_lo, int KT, int passes)
+// (a multiple of 32). Per round of BS paths every lane walks the pass with
+// its factors started at S^m, so that the walk's values are S^m phi_k(U^m);
+// per tile of 32 positions the lane values are reduce-scattered over the
+// warp and added to the warp's accumulators in shared memory, which are
+// summed in fixed warp order at the end.
+template <typename R, int D>
+__global__ void __launch_bounds__(kCosBS, sizeof(R) == 4 ? 4 : 2) k_project_cos(const __grid_constant__ QrParams P,
+                                                           const CosGroup* __restrict__ G,
+                                                           const uint4* __restrict__ flags, int ngroups,
+                                                           const R* __restrict__ S, double* __restrict__ partial,
+                                                           long long row_stride, int i_lo, int KT, int passes)
 {
+    constexpr int BS = kCosBS, W = BS / 32;
     extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int W = BS / 32;
-    const int K1p = P.K1;
-    R* tab = reinterpret_cast<R*>(smem);
-    R* wacc = reinterpret_cast<R*>(smem + cos_table_bytes<R>(D, K1p, BS));
+    R* wacc = reinterpret_cast<R*>(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int per_row = P.n_chunks * passes;
     const int ii = (int)(blockIdx.x / per_row), rem = (int)(blockIdx.x % per_row);
     const int ps = rem / P.n_chunks, ch = rem % P.n_chunks;
     const int i = i_lo + ii;
     const int gs = ps * (KT / 4);
-    const int ge = min(ngroups, gs + KT / 4);  // both multiples of 8
+    const int ge = min(ngroups, gs + KT / 4);  // both multiples of 16
     R* myacc = wacc + (size_t)warp * KT;
     for (int q = lane; q < KT; q += 32) myacc[q] = (R)0;
     __syncwarp();
 
-    R* mytab = tab + tid;
-    const R* tl = mytab + (size_t)(D - 1) * K1p * BS;
+    const uint4 q0 = __ldg(G + gs);
+    const int a00 = (int)(q0.x & 0xffffu);
     const int rounds = P.chunk / BS;
     for (int r = 0; r < rounds; ++r) {
         const long long m = (long long)ch * P.chunk + (long long)r * BS + tid;
@@ -322,22 +411,24 @@ __global__ void __launch_bounds__(BS) k_project_cos(const __grid_constant__ QrPa
         const R Sv = active ? S[(size_t)ii * (size_t)P.M + (size_t)m] : (R)0;
         V2<R> ph[D];
         start_phases_dev<R, D>(P, i, active ? m : 0, ph);  // e^{i pi U^m} (half angle)
-        fill_cos<R, D, BS>(mytab, K1p, ph);
-        R b[D];
-        const uint4 q0 = __ldg(G + gs);
-        R p = prefix_update<R, D, BS>(b, Sv, 0, q0.z, q0.w, mytab, K1p);
+        CosWalk<R, D> Wk;
+        Wk.init(ph, Sv);
+        Wk.seek(q0.z, q0.w, a00, Sv);
         for (int g0 = gs; g0 < ge; g0 += 8) {
+            const uint2 fl = __ldg(reinterpret_cast<const uint2*>(flags) + g0 / 8);
             R v[32];
 #pragma unroll
             for (int gg = 0; gg < 8; ++gg) {
-                const uint4 q = __ldg(G + g0 + gg);
-                const int a0 = (int)(q.x & 0xffffu), f = (int)(q.x >> 16);
-                if (D > 1 && f < D - 1) p = prefix_update<R, D, BS>(b, Sv, f, q.z, q.w, mytab, K1p);
-                const R* ta = tl + (size_t)a0 * BS;
-                v[4 * gg + 0] = p * ta[0];
-                v[4 * gg + 1] = p * ta[BS];
-                v[4 * gg + 2] = p * ta[2 * BS];
-                v[4 * gg + 3] = p * ta[3 * BS];
+                const uint32_t fb = ((gg < 4 ? fl.x : fl.y) >> (8 * (gg & 3))) & 0xffu;
+                const bool start = (fb & 0x80u) != 0;
+                // (the pass's first group: seek placed the walk on its run already)
+                if (D > 1 && start && (int)(fb & 7u) < D - 1 && g0 + gg != gs) Wk.new_run((int)(fb & 7u), Sv);
+                R v0, v1, v2, v3;
+                Wk.values(start, v0, v1, v2, v3);
+                v[4 * gg + 0] = Wk.p * v0;
+                v[4 * gg + 1] = Wk.p * v1;
+                v[4 * gg + 2] = Wk.p * v2;
+                v[4 * gg + 3] = Wk.p * v3;
             }
             const R s = cos_fold32<R>(v, lane);
             myacc[(g0 - gs) * 4 + lane] += s;
@@ -396,14 +487,13 @@ __global__ void k_pack_cos(const double2* __restrict__ alpha, int nG, const int*
     packed[(size_t)i * row_stride + pos[e]] = (R)alpha[(size_t)i * nG + e].x;
 }
 
-template <typename R, int D, int BS>
-__global__ void __launch_bounds__(BS) k_eval_cos(const __grid_constant__ QrParams P, const CosGroup* __restrict__ G,
-                                                 int ng, const R* __restrict__ crow, const double* __restrict__ xs,
-                                                 long long n, double* __restrict__ ys, int use_g)
+template <typename R, int D>
+__global__ void __launch_bounds__(kCosBS) k_eval_cos(const __grid_constant__ QrParams P,
+                                                     const uint4* __restrict__ flags, int ng,
+                                                     const R* __restrict__ crow, const double* __restrict__ xs,
+                                                     long long n, double* __restrict__ ys, int use_g)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    R* tab = reinterpret_cast<R*>(smem);
-    const long long p = (long long)blockIdx.x * BS + threadIdx.x;
+    const long long p = (long long)blockIdx.x * kCosBS + threadIdx.x;
     if (p >= n) return;
     R x[D];
 #pragma unroll
@@ -415,100 +505,75 @@ __global__ void __launch_bounds__(BS) k_eval_cos(const __grid_constant__ QrParam
     V2<R> zz[D];
 #pragma unroll
     for (int l = 0; l < D; ++l) zz[l] = nu_phase<R>(P, x[l]);
-    R* mytab = tab + threadIdx.x;
-    fill_cos<R, D, BS>(mytab, P.K1, zz);
-    ys[p] = (double)cos_series<R, D, BS>(crow, G, ng, mytab, P.K1);
+    CosWalk<R, D> W;
+    W.init(zz, (R)1);
+    ys[p] = (double)cos_series<R, D>(crow, flags, ng, W);
 }
 
 // ------------------------------------------------------------ launchers
 namespace {
 
 constexpr size_t kCap = 227 * 1024;
+// rows staged in shared memory only while four blocks per SM still fit
+constexpr size_t kRowsSmemMax = 52 * 1024;
 
-template <typename R, int D, int BS, bool CG>
-cudaError_t paths_cos_bs(const QrParams& P, const CosGroup* G, int ng, const void* packed, long long row_stride,
+template <typename R, int D, bool CG>
+cudaError_t paths_cos_cg(const QrParams& P, const uint4* flags, int ng, const void* packed, long long row_stride,
                          void* S, int i_lo, int i_hi, unsigned long long* counters, unsigned* status, cudaStream_t st)
 {
-    const size_t sm = cos_paths_smem<R>(D, P.K1, row_stride, BS, CG);
-    if (sm > kCap) return cudaErrorInvalidConfiguration;
-    auto kern = k_paths_cos<R, D, BS, CG>;
+    constexpr int BS = kCosBS;
+    const size_t sm = cos_paths_smem<R>(row_stride, CG);
+    auto kern = k_paths_cos<R, D, CG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int tiles = (int)((P.M + BS - 1) / BS);
     const long long blocks = (long long)tiles * (i_hi - i_lo);
     if (blocks <= 0) return cudaSuccess;
-    kern<<<(unsigned)blocks, BS, sm, st>>>(P, G, ng, static_cast<const R*>(packed), row_stride, static_cast<R*>(S),
-                                           i_lo, tiles, counters, status);
+    kern<<<(unsigned)blocks, BS, sm, st>>>(P, flags, ng, static_cast<const R*>(packed), row_stride,
+                                           static_cast<R*>(S), i_lo, tiles, counters, status);
     return cudaGetLastError();
 }
 
-// 128-thread blocks with both coefficient rows in shared memory when they fit
-// beside the tables, else rows from global memory; 64 threads when the
-// tables alone do not fit 128 lanes
 template <typename R, int D>
-cudaError_t paths_cos_t(const QrParams& P, const CosGroup* G, int ng, const void* packed, long long row_stride,
+cudaError_t paths_cos_t(const QrParams& P, const uint4* flags, int ng, const void* packed, long long row_stride,
                         void* S, int i_lo, int i_hi, unsigned long long* counters, unsigned* status, cudaStream_t st)
 {
-    if (cos_paths_smem<R>(D, P.K1, row_stride, 128, false) <= kCap)
-        return paths_cos_bs<R, D, 128, false>(P, G, ng, packed, row_stride, S, i_lo, i_hi, counters, status, st);
-    if (cos_paths_smem<R>(D, P.K1, row_stride, 128, true) <= kCap)
-        return paths_cos_bs<R, D, 128, true>(P, G, ng, packed, row_stride, S, i_lo, i_hi, counters, status, st);
-    return paths_cos_bs<R, D, 64, true>(P, G, ng, packed, row_stride, S, i_lo, i_hi, counters, status, st);
+    if (cos_paths_smem<R>(row_stride, false) <= kRowsSmemMax)
+        return paths_cos_cg<R, D, false>(P, flags, ng, packed, row_stride, S, i_lo, i_hi, counters, status, st);
+    return paths_cos_cg<R, D, true>(P, flags, ng, packed, row_stride, S, i_lo, i_hi, counters, status, st);
 }
 
-template <typename R, int D, int BS>
-cudaError_t project_cos_bs(const QrParams& P, const CosGroup* G, int ngroups, const void* S, double* partial,
-                           long long row_stride, int i_lo, int i_hi, cudaStream_t st)
+template <typename R, int D>
+cudaError_t project_cos_t(const QrParams& P, const CosGroup* G, const uint4* flags, int ngroups, const void* S,
+                          double* partial, long long row_stride, int i_lo, int i_hi, cudaStream_t st)
 {
-    constexpr int W = BS / 32;
-    const size_t tb = cos_table_bytes<R>(D, P.K1, BS);
-    if (tb + (size_t)W * 32 * sizeof(R) > kCap) return cudaErrorInvalidConfiguration;
-    // about 3 CTAs per SM where the tables allow it, else at least 1024
-    // positions per pass (every pass rebuilds the tables of all its paths)
-    const size_t budget = std::min(kCap, std::max((size_t)76 * 1024, tb + (size_t)W * 1024 * sizeof(R)));
-    long long KT = (long long)((budget - tb) / (W * sizeof(R))) & ~31ll;
-    if (KT > row_stride) KT = row_stride;
+    constexpr int W = kCosBS / 32;
+    // per-warp accumulators of up to 2048 positions (32 KB in FP32); every
+    // pass walks its paths from their start points again (KT and the pass
+    // starts are multiples of 64 positions: whole words of flags)
+    long long KT = std::min<long long>(row_stride, 2048);
     const int passes = (int)((row_stride + KT - 1) / KT);
-    const size_t sm = tb + (size_t)W * KT * sizeof(R);
-    auto kern = k_project_cos<R, D, BS>;
+    const size_t sm = (size_t)W * KT * sizeof(R);
+    if (sm > kCap) return cudaErrorInvalidConfiguration;
+    auto kern = k_project_cos<R, D>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const long long blocks = (long long)P.n_chunks * passes * (i_hi - i_lo);
     if (blocks <= 0) return cudaSuccess;
-    kern<<<(unsigned)blocks, BS, sm, st>>>(P, G, ngroups, static_cast<const R*>(S), partial, row_stride, i_lo,
-                                           (int)KT, passes);
+    kern<<<(unsigned)blocks, kCosBS, sm, st>>>(P, G, flags, ngroups, static_cast<const R*>(S), partial, row_stride,
+                                               i_lo, (int)KT, passes);
     return cudaGetLastError();
 }
 
 template <typename R, int D>
-cudaError_t project_cos_t(const QrParams& P, const CosGroup* G, int ngroups, const void* S, double* partial,
-                          long long row_stride, int i_lo, int i_hi, cudaStream_t st)
-{
-    if (cos_table_bytes<R>(D, P.K1, 128) + 4 * 32 * sizeof(R) <= kCap)
-        return project_cos_bs<R, D, 128>(P, G, ngroups, S, partial, row_stride, i_lo, i_hi, st);
-    return project_cos_bs<R, D, 64>(P, G, ngroups, S, partial, row_stride, i_lo, i_hi, st);
-}
-
-template <typename R, int D, int BS>
-cudaError_t eval_cos_bs(const QrParams& P, const CosGroup* G, int ng, const void* row, const double* x, long long n,
-                        double* y, int use_g, cudaStream_t st)
-{
-    const size_t sm = cos_table_bytes<R>(D, P.K1, BS);
-    if (sm > kCap) return cudaErrorInvalidConfiguration;
-    auto kern = k_eval_cos<R, D, BS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    if (n <= 0) return cudaSuccess;
-    kern<<<(unsigned)((n + BS - 1) / BS), BS, sm, st>>>(P, G, ng, static_cast<const R*>(row), x, n, y, use_g);
-    return cudaGetLastError();
-}
-
-template <typename R, int D>
-cudaError_t eval_cos_t(const QrParams& P, const CosGroup* G, int ng, const void* row, const double* x, long long n,
+cudaError_t eval_cos_t(const QrParams& P, const uint4* flags, int ng, const void* row, const double* x, long long n,
                        double* y, int use_g, cudaStream_t st)
 {
-    if (cos_table_bytes<R>(D, P.K1, 128) <= kCap) return eval_cos_bs<R, D, 128>(P, G, ng, row, x, n, y, use_g, st);
-    return eval_cos_bs<R, D, 64>(P, G, ng, row, x, n, y, use_g, st);
+    if (n <= 0) return cudaSuccess;
+    k_eval_cos<R, D><<<(unsigned)((n + kCosBS - 1) / kCosBS), kCosBS, 0, st>>>(P, flags, ng,
+                                                                              static_cast<const R*>(row), x, n, y,
+                                                                              use_g);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -526,31 +591,26 @@ cudaError_t eval_cos_t(const QrParams& P, const CosGroup* G, int ng, const void*
     default: return cudaErrorInvalidValue; \
     }
 
-size_t cos_paths_smem_min(int prec, int d, int K1p)
-{
-    const size_t sm = prec == QR_FP32 ? cos_paths_smem<float>(d, K1p, 0, 64, true)
-                                      : cos_paths_smem<double>(d, K1p, 0, 64, true);
-    return sm <= kCap ? sm : 0;
-}
-
-cudaError_t launch_paths_cos(int prec, const QrParams& P, const CosGroup* groups, int ngroups, const void* packed,
+cudaError_t launch_paths_cos(int prec, const QrParams& P, const uint8_t* flags, int ngroups, const void* packed,
                              long long row_stride, void* S, int i_lo, int i_hi, unsigned long long* counters,
                              unsigned* status, cudaStream_t st)
 {
+    const uint4* fl = reinterpret_cast<const uint4*>(flags);
     if (prec == QR_FP32) {
-        QR_COS_DISPATCH(paths_cos_t, float, P, groups, ngroups, packed, row_stride, S, i_lo, i_hi, counters, status,
-                        st)
+        QR_COS_DISPATCH(paths_cos_t, float, P, fl, ngroups, packed, row_stride, S, i_lo, i_hi, counters, status, st)
     }
-    QR_COS_DISPATCH(paths_cos_t, double, P, groups, ngroups, packed, row_stride, S, i_lo, i_hi, counters, status, st)
+    QR_COS_DISPATCH(paths_cos_t, double, P, fl, ngroups, packed, row_stride, S, i_lo, i_hi, counters, status, st)
 }
 
-cudaError_t launch_project_cos(int prec, const QrParams& P, const CosGroup* groups, int ngroups, const void* S,
-                               double* partial, long long row_stride, int i_lo, int i_hi, cudaStream_t st)
+cudaError_t launch_project_cos(int prec, const QrParams& P, const CosGroup* groups, const uint8_t* flags, int ngroups,
+                               const void* S, double* partial, long long row_stride, int i_lo, int i_hi,
+                               cudaStream_t st)
 {
+    const uint4* fl = reinterpret_cast<const uint4*>(flags);
     if (prec == QR_FP32) {
-        QR_COS_DISPATCH(project_cos_t, float, P, groups, ngroups, S, partial, row_stride, i_lo, i_hi, st)
+        QR_COS_DISPATCH(project_cos_t, float, P, groups, fl, ngroups, S, partial, row_stride, i_lo, i_hi, st)
     }
-    QR_COS_DISPATCH(project_cos_t, double, P, groups, ngroups, S, partial, row_stride, i_lo, i_hi, st)
+    QR_COS_DISPATCH(project_cos_t, double, P, groups, fl, ngroups, S, partial, row_stride, i_lo, i_hi, st)
 }
 
 cudaError_t launch_reduce_cos(int prec, const QrParams& P, const double* partial, const int* pos, double2* alpha,
@@ -582,13 +642,14 @@ cudaError_t launch_pack_cos(int prec, const double2* alpha, int nG, const int* p
     return cudaGetLastError();
 }
 
-cudaError_t launch_eval_cos(int prec, const QrParams& P, const CosGroup* groups, int ngroups, const void* packed_row,
+cudaError_t launch_eval_cos(int prec, const QrParams& P, const uint8_t* flags, int ngroups, const void* packed_row,
                             const double* x, long long n, double* y, int use_g, cudaStream_t st)
 {
+    const uint4* fl = reinterpret_cast<const uint4*>(flags);
     if (prec == QR_FP32) {
-        QR_COS_DISPATCH(eval_cos_t, float, P, groups, ngroups, packed_row, x, n, y, use_g, st)
+        QR_COS_DISPATCH(eval_cos_t, float, P, fl, ngroups, packed_row, x, n, y, use_g, st)
     }
-    QR_COS_DISPATCH(eval_cos_t, double, P, groups, ngroups, packed_row, x, n, y, use_g, st)
+    QR_COS_DISPATCH(eval_cos_t, double, P, fl, ngroups, packed_row, x, n, y, use_g, st)
 }
 
 }  // namespace qr

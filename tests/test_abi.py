@@ -66,7 +66,7 @@ def _init(lib, d=2, N=4, T=1.0, gamma=(1, 2), M=64, prec=0, fkind=0, gkind=0, nu
     (dict(T=-1.0), "T must"), (dict(M=0), "M must"), (dict(prec=7), "precision"),
     (dict(gamma=(6, 2)), "index set"), (dict(gamma=(5, 0)), "index set"), (dict(d=5, gamma=(2, 128)), "|k_l| <= 127"),
     (dict(d=1, gamma=(0, 40000)), "|k_l| <= 32767"),
-    (dict(d=1, gamma=(3, 120), kern=1), "unfolded set"), (dict(d=1, gamma=(3, 40000)), "direct cosine kernels"),
+    (dict(d=1, gamma=(3, 120), kern=1), "unfolded set"), (dict(d=1, gamma=(3, 70000)), "direct cosine kernels"),
     (dict(kern=2), "needs a cosine index set"), (dict(kern=5), "unknown path kernel"), (dict(nu=(0, -1.0)), "mu"),
     (dict(fkind=9), "driver"), (dict(gkind=9), "terminal"), (dict(lattice=3, M=10), "lattice"),
 ])
