@@ -78,19 +78,26 @@ typedef struct {
  * with the complex Fourier basis phi_k(x) = e^{2 pi i k.F_nu(x)}. Kinds 3-5
  * are the N^d sets of Sec. 2.4.2 with the paper's cosine basis
  * phi_k(x) = prod_l C_{k_l}(F_nu(x_l)), C_0 = 1, C_k = sqrt(2) cos(k pi u)
- * (Lemma ortho:dim1). Internally a cosine context works on the unfolded set
- * {m in Z^d : |m| in Gamma} (Gamma_F(n) -> kind 0, Gamma_T(n) -> kind 1,
- * Gamma_H(n) -> kind 2, same n) with half-angle phases e^{i pi m.F_nu(x)}:
- * a cosine series sum_k a_k phi_k equals Re sum_m c_m e^{i pi m.F_nu(x)} with
- * real, sign-symmetric c_m = a_|m| 2^{-d'(m)/2}, d'(m) = #{l : m_l != 0},
- * and after every projection the coefficients are averaged over the sign
- * orbits, which is the cosine projection of eq. (Aqi:bar:M) in these
- * coordinates. qr_gamma_size/list, qr_get/set_coefs and a QR_GT_TRIGPOLY g
+ * (Lemma ortho:dim1). A cosine context runs one of two routes (see
+ * qr_opts.path_kernel):
+ *   direct: real kernels on Gamma itself, each factor C_k stepped by one
+ *     complex product along the canonical order (runs of k_d = 0, 1, ...
+ *     under a common prefix; the next run's prefix has one coordinate one
+ *     larger and the later ones 0, true of every downward-closed set);
+ *     prefix coordinates k_1..k_{d-1} <= 255 and k_d <= 65532;
+ *   unfolded: the set {m in Z^d : |m| in Gamma} (Gamma_F(n) -> kind 0,
+ *     Gamma_T(n) -> kind 1, Gamma_H(n) -> kind 2, same n) on the Fourier
+ *     kernels with half-angle phases e^{i pi m.F_nu(x)}: a cosine series
+ *     sum_k a_k phi_k equals Re sum_m c_m e^{i pi m.F_nu(x)} with real,
+ *     sign-symmetric c_m = a_|m| 2^{-d'(m)/2}, d'(m) = #{l : m_l != 0}, and
+ *     after every projection the coefficients are averaged over the sign
+ *     orbits, which is the cosine projection of eq. (Aqi:bar:M) in these
+ *     coordinates; its per-lane power tables of d (max|k_l| + 1) complex
+ *     values must fit in shared memory (QR_ENOTIMPL otherwise).
+ * Either way qr_gamma_size/list, qr_get/set_coefs and a QR_GT_TRIGPOLY g
  * use Gamma itself (the N^d set) and the cosine coefficients a_k: real
  * values in the interleaved complex layout (imaginary parts 0 on output,
- * ignored on input). Canonical order: lexicographic, k_1 most significant. The
- * generic kernels hold per-lane power tables of d (max|k_l| + 1) complex
- * values in shared memory; qr_init returns QR_ENOTIMPL when they exceed it. */
+ * ignored on input). Canonical order: lexicographic, k_1 most significant. */
 enum {
     QR_G_LINF = 0,      /* max_l |k_l| <= n */
     QR_G_L1 = 1,        /* sum_l |k_l| <= n */
@@ -145,7 +152,11 @@ typedef struct {
     int instance;             /* Philox counter field, 0 <= instance < 4096 */
     int path_kernel;          /* 0: the compile-time tree kernel when one is built for this
                                  index set (|k|_1 or |k|_inf sets of the benchmark workloads),
-                                 else the table-driven kernel; 1: always the table-driven kernel */
+                                 else the table-driven kernel; cosine sets: the unfolded
+                                 route when a tree kernel covers the unfolded set, else
+                                 the direct route. 1: always the table-driven kernel
+                                 (cosine: the unfolded route). 2: the direct route (cosine
+                                 sets only; QR_EINVAL for kinds 0-2). Other values: QR_EINVAL */
     double damping_q;         /* damping exponent q >= 0 of eq. (yqi), 0 = none: the
                                  coefficients represent ybar^q = y / (1 + |x|^2)^{q/2};
                                  responses follow eq. (Sqi:bar:M) (the series at X_{j+1}
@@ -159,7 +170,8 @@ typedef struct {
  *   d in [1, 8]; N in [1, 256]; T > 0; b: d doubles (host); sigma: d*d doubles,
  *   row-major (host), X_{j+1} = X_j + b dt + sigma sqrt(dt) Z; every |k_l| <= 32767
  *   for d <= 4 and <= 127 above (QR_ENOTIMPL otherwise, or when the generic
- *   kernels' per-lane power tables and coefficient rows exceed shared memory).
+ *   kernels' per-lane power tables and coefficient rows exceed shared memory);
+ *   the direct cosine route has its own limits (see the index-set kinds).
  *   opts may be NULL: M = 2^14, seed 1, QR_FP64, no truncation. */
 qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const qr_gamma* gamma,
                   const double* b, const double* sigma, const qr_fn* f, const qr_fn* g,

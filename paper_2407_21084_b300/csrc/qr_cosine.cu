@@ -376,13 +376,15 @@ __global__ void __launch_bounds__(kCosBS, sizeof(R) == 4 ? 4 : 2) k_paths_cos(co
 
 // --------------------------------------------------------- projection kernel
 // One CTA: row i, a chunk of P.chunk paths, a pass of KT packed positions
-// (a multiple of 32). Per round of BS paths every lane walks the pass with
-// its factors started at S^m, so that the walk's values are S^m phi_k(U^m);
-// per tile of 32 positions the lane values are reduce-scattered over the
-// warp and added to the warp's accumulators in shared memory, which are
+// (a multiple of 32). Per round of PPL*BS paths every lane walks the pass
+// with PPL paths, their factors started at S^m, so that the walks' values
+// are S^m phi_k(U^m); per tile of 32 positions the lane's sums over its
+// paths are reduce-scattered over the warp (one 31-shuffle fold for PPL
+// paths) and added to the warp's accumulators in shared memory, which are
 // summed in fixed warp order at the end.
-template <typename R, int D>
-__global__ void __launch_bounds__(kCosBS, sizeof(R) == 4 ? 4 : 2) k_project_cos(const __grid_constant__ QrParams P,
+template <typename R, int D, int PPL>
+__global__ void __launch_bounds__(kCosBS, PPL == 2 ? 3 : (sizeof(R) == 4 ? 4 : 2))
+    k_project_cos(const __grid_constant__ QrParams P,
                                                            const CosGroup* __restrict__ G,
                                                            const uint4* __restrict__ flags, int ngroups,
                                                            const R* __restrict__ S, double* __restrict__ partial,
@@ -404,16 +406,20 @@ __global__ void __launch_bounds__(kCosBS, sizeof(R) == 4 ? 4 : 2) k_project_cos(
 
     const uint4 q0 = __ldg(G + gs);
     const int a00 = (int)(q0.x & 0xffffu);
-    const int rounds = P.chunk / BS;
+    const int rounds = P.chunk / (PPL * BS);
     for (int r = 0; r < rounds; ++r) {
-        const long long m = (long long)ch * P.chunk + (long long)r * BS + tid;
-        const bool active = m < P.M;
-        const R Sv = active ? S[(size_t)ii * (size_t)P.M + (size_t)m] : (R)0;
-        V2<R> ph[D];
-        start_phases_dev<R, D>(P, i, active ? m : 0, ph);  // e^{i pi U^m} (half angle)
-        CosWalk<R, D> Wk;
-        Wk.init(ph, Sv);
-        Wk.seek(q0.z, q0.w, a00, Sv);
+        CosWalk<R, D> Wk[PPL];
+        R Sv[PPL];
+#pragma unroll
+        for (int u = 0; u < PPL; ++u) {
+            const long long m = (long long)ch * P.chunk + (long long)(r * PPL + u) * BS + tid;
+            const bool active = m < P.M;
+            Sv[u] = active ? S[(size_t)ii * (size_t)P.M + (size_t)m] : (R)0;
+            V2<R> ph[D];
+            start_phases_dev<R, D>(P, i, active ? m : 0, ph);  // e^{i pi U^m} (half angle)
+            Wk[u].init(ph, Sv[u]);
+            Wk[u].seek(q0.z, q0.w, a00, Sv[u]);
+        }
         for (int g0 = gs; g0 < ge; g0 += 8) {
             const uint2 fl = __ldg(reinterpret_cast<const uint2*>(flags) + g0 / 8);
             R v[32];
@@ -421,14 +427,25 @@ __global__ void __launch_bounds__(kCosBS, sizeof(R) == 4 ? 4 : 2) k_project_cos(
             for (int gg = 0; gg < 8; ++gg) {
                 const uint32_t fb = ((gg < 4 ? fl.x : fl.y) >> (8 * (gg & 3))) & 0xffu;
                 const bool start = (fb & 0x80u) != 0;
-                // (the pass's first group: seek placed the walk on its run already)
-                if (D > 1 && start && (int)(fb & 7u) < D - 1 && g0 + gg != gs) Wk.new_run((int)(fb & 7u), Sv);
-                R v0, v1, v2, v3;
-                Wk.values(start, v0, v1, v2, v3);
-                v[4 * gg + 0] = Wk.p * v0;
-                v[4 * gg + 1] = Wk.p * v1;
-                v[4 * gg + 2] = Wk.p * v2;
-                v[4 * gg + 3] = Wk.p * v3;
+#pragma unroll
+                for (int u = 0; u < PPL; ++u) {
+                    // (the pass's first group: seek placed the walk on its run already)
+                    if (D > 1 && start && (int)(fb & 7u) < D - 1 && g0 + gg != gs)
+                        Wk[u].new_run((int)(fb & 7u), Sv[u]);
+                    R v0, v1, v2, v3;
+                    Wk[u].values(start, v0, v1, v2, v3);
+                    if (u == 0) {
+                        v[4 * gg + 0] = Wk[u].p * v0;
+                        v[4 * gg + 1] = Wk[u].p * v1;
+                        v[4 * gg + 2] = Wk[u].p * v2;
+                        v[4 * gg + 3] = Wk[u].p * v3;
+                    } else {
+                        v[4 * gg + 0] = fma(Wk[u].p, v0, v[4 * gg + 0]);
+                        v[4 * gg + 1] = fma(Wk[u].p, v1, v[4 * gg + 1]);
+                        v[4 * gg + 2] = fma(Wk[u].p, v2, v[4 * gg + 2]);
+                        v[4 * gg + 3] = fma(Wk[u].p, v3, v[4 * gg + 3]);
+                    }
+                }
             }
             const R s = cos_fold32<R>(v, lane);
             myacc[(g0 - gs) * 4 + lane] += s;
@@ -543,9 +560,9 @@ cudaError_t paths_cos_t(const QrParams& P, const uint4* flags, int ng, const voi
     return paths_cos_cg<R, D, true>(P, flags, ng, packed, row_stride, S, i_lo, i_hi, counters, status, st);
 }
 
-template <typename R, int D>
-cudaError_t project_cos_t(const QrParams& P, const CosGroup* G, const uint4* flags, int ngroups, const void* S,
-                          double* partial, long long row_stride, int i_lo, int i_hi, cudaStream_t st)
+template <typename R, int D, int PPL>
+cudaError_t project_cos_ppl(const QrParams& P, const CosGroup* G, const uint4* flags, int ngroups, const void* S,
+                            double* partial, long long row_stride, int i_lo, int i_hi, cudaStream_t st)
 {
     constexpr int W = kCosBS / 32;
     // per-warp accumulators of up to 2048 positions (32 KB in FP32); every
@@ -555,7 +572,7 @@ cudaError_t project_cos_t(const QrParams& P, const CosGroup* G, const uint4* fla
     const int passes = (int)((row_stride + KT - 1) / KT);
     const size_t sm = (size_t)W * KT * sizeof(R);
     if (sm > kCap) return cudaErrorInvalidConfiguration;
-    auto kern = k_project_cos<R, D>;
+    auto kern = k_project_cos<R, D, PPL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const long long blocks = (long long)P.n_chunks * passes * (i_hi - i_lo);
@@ -563,6 +580,17 @@ cudaError_t project_cos_t(const QrParams& P, const CosGroup* G, const uint4* fla
     kern<<<(unsigned)blocks, kCosBS, sm, st>>>(P, G, flags, ngroups, static_cast<const R*>(S), partial, row_stride,
                                                i_lo, (int)KT, passes);
     return cudaGetLastError();
+}
+
+// two paths per lane (one fold for both) in FP32, where the two walks fit
+// the registers of 3 blocks per SM (at most 160 for d <= 8)
+template <typename R, int D>
+cudaError_t project_cos_t(const QrParams& P, const CosGroup* G, const uint4* flags, int ngroups, const void* S,
+                          double* partial, long long row_stride, int i_lo, int i_hi, cudaStream_t st)
+{
+    if (sizeof(R) == 4 && P.chunk % (2 * kCosBS) == 0)
+        return project_cos_ppl<R, D, 2>(P, G, flags, ngroups, S, partial, row_stride, i_lo, i_hi, st);
+    return project_cos_ppl<R, D, 1>(P, G, flags, ngroups, S, partial, row_stride, i_lo, i_hi, st);
 }
 
 template <typename R, int D>
