@@ -69,14 +69,16 @@ def _problem(d, kind, n, delta, M, seed, q=0.0):
     return W.Sec5Problem(d=d, N=int(round(1.0 / delta)), gamma_kind=kind, gamma_n=n, M=M, seed=seed, q=q)
 
 
-def run_row(row, runs: int, ci_runs: int, precision=L.QR_FP32, path_kernel=0):
+def run_row(row, runs: int, ci_runs: int, precision=L.QR_FP32, path_kernel=0, paths=None, profile=False):
     import torch
 
     from .solver import Solver
 
     label, d, kind, n, ng, delta, M, gpu_s, paper_mse, ci = row[:10]
+    if paths:
+        M = paths
     paper_gpus = row[10] if len(row) > 10 else 1
-    times, mse = [], {}
+    times, mse, split = [], {}, []
     for q in paper_mse:
         per = []
         for r in range(runs):
@@ -84,12 +86,17 @@ def run_row(row, runs: int, ci_runs: int, precision=L.QR_FP32, path_kernel=0):
             with Solver.from_sec5(p, precision=precision, path_kernel=path_kernel) as s:
                 k, _ = s.cosine_coefs()
                 assert len(k) == ng, (label, len(k), ng)
+                if profile:
+                    s.set_profiling(True)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 s.backward_sweep()
                 torch.cuda.synchronize()
                 if q == min(paper_mse):
                     times.append(time.perf_counter() - t0)
+                    if profile:
+                        st = s.stats()
+                        split.append({k: st[k] for k in ("ms_paths", "ms_project", "ms_reduce")})
                 per.append(s.mse_indicators(lambda t, x: p.exact_u(t, x), n=1000))
         mse[str(q)] = {"mse_max": float(np.mean([m["mse_max"] for m in per])),
                        "mse_av": float(np.mean([m["mse_av"] for m in per])),
@@ -103,6 +110,13 @@ def run_row(row, runs: int, ci_runs: int, precision=L.QR_FP32, path_kernel=0):
            "paper_gpu_s": gpu_s, "paper_gpu_evals_per_s": work / gpu_s, "speedup_vs_paper_gpu": gpu_s / t,
            "paper_hardware": "%dx GeForce GTX TITAN Black (Kepler GK110), FP32, CUDA 7.5" % paper_gpus,
            "path_kernel": path_kernel, "mse_by_q": mse, "runs": runs}
+    if paths:
+        out["speedup_vs_paper_gpu"] = None
+        out["note"] = "M overridden: the time is not comparable with the paper's"
+    if profile:
+        # per-kernel device time of the timed sweeps (events on the library's
+        # stream, one synchronisation per kernel: the sweep is then slower)
+        out["kernel_ms"] = split
     if ci is not None and ci_runs > 0:
         vals = []
         for r in range(ci_runs):
@@ -124,6 +138,8 @@ def main():
     ap.add_argument("--runs", type=int, default=3, help="independent runs per row for time and MSE")
     ap.add_argument("--ci-runs", type=int, default=50, help="runs for the d = 1 confidence intervals")
     ap.add_argument("--max-gpu-s", type=float, default=3000.0, help="skip rows the paper timed above this")
+    ap.add_argument("--paths", type=int, default=0, help="override M of every row (0: the paper's M)")
+    ap.add_argument("--profile", action="store_true", help="record per-kernel device times of the timed sweeps")
     ap.add_argument("--path-kernel", type=int, default=0,
                     help="0: automatic; 1: the unfolded set on the Fourier kernels; 2: the direct cosine kernels")
     args = ap.parse_args()
@@ -132,7 +148,8 @@ def main():
         if not any(row[0].startswith(w) for w in want) or row[7] > args.max_gpu_s:
             continue
         try:
-            out = run_row(row, args.runs, args.ci_runs, path_kernel=args.path_kernel)
+            out = run_row(row, args.runs, args.ci_runs, path_kernel=args.path_kernel, paths=args.paths or None,
+                          profile=args.profile)
         except L.QrError as e:  # e.g. an unfolded set too large for the generic kernels' shared memory
             out = {"row": row[0], "skipped": str(e)}
         print(json.dumps(out), flush=True)
