@@ -192,11 +192,19 @@ template <typename R, int D, int NN, int KIND>
 static cudaError_t project_tree_t(const QrParams& P, const void* S, const int* perm, double2* partial, int i_lo,
                                   int i_hi, cudaStream_t st)
 {
-    constexpr int BS = 128;
-    constexpr int SC = sizeof(R) == 4 ? 1024 : 512;
+#ifndef QR_PROJ_BS32
+#define QR_PROJ_BS32 128
+#endif
+#ifndef QR_PROJ_SC32
+#define QR_PROJ_SC32 1024
+#endif
+    constexpr int BS = sizeof(R) == 4 ? QR_PROJ_BS32 : 128;
+    constexpr int SC = sizeof(R) == 4 ? QR_PROJ_SC32 : 512;
     using SM = ProjSmem<R, D, FullTree<D, NN, KIND>, BS, SC>;
     const size_t sm = sizeof(SM);
-    if (sm > 227 * 1024 || P.chunk % SC != 0 && P.chunk > SC) return cudaErrorInvalidConfiguration;
+    // a chunk need not be a multiple of SC: its last block is partly empty
+    // (zero responses, no contribution)
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
     auto kern = k_project_tree<R, D, NN, KIND, BS, SC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

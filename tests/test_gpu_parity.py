@@ -123,6 +123,24 @@ def test_c2_prefix_matches_oracle(qr, ora, prec, M, kern):
         assert relerr(s.coefs(), a_ref) < TOL[prec] * (1 if M >= 4096 else 10)
 
 
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_c2_ragged_projection_chunks_match_oracle(qr, ora, prec):
+    """C2 at M = 270000: the projection's chunk of paths (256 * ceil(M / 65536)
+    = 1280 in FP32, 128 * ceil(M / 32768) = 1152 in FP64) is not a multiple
+    of the tiled kernel's block of paths, so every chunk ends with a partly
+    empty block. Two iterations, rows N-3 .. N-1 against the oracle."""
+    w = W.c2()
+    M = 270000
+    p = ora_problem(ora, w, M=M)
+    rows = (w.N - 3, w.N)
+    a1, _ = ora.picard_iter(p, p.zeros(), i_range=rows)
+    a2, _ = ora.picard_iter(p, a1, i_range=rows)
+    with _solver(qr, w, prec, M=M, kern=TREE) as s:
+        s.picard_step(2)
+        a = s.coefs()
+    assert relerr(a[rows[0]:], a2[rows[0]:]) < TOL[prec]
+
+
 def test_picard_N_equals_backward_sweep_and_is_deterministic(qr, ora):
     w = W.c1().with_(N=4)
     with _solver(qr, w, FP64, M=2048) as s:
