@@ -91,9 +91,23 @@ __device__ __forceinline__ void normals_fast(const QrParams& P, int i, uint32_t 
 #pragma unroll
         for (int c = 0; 2 * c < D; ++c) {
             const uint4 r = philox4x32_10(make_uint4(m, (uint32_t)c, (uint32_t)j, ctr_hi(P.instance, QR_TAG_INCR, i)), key);
-            // ln(u_a): u_a < 1/2 iff the top bit of r.x is clear; above 1/2 use log1p(-(1 - u_a)),
-            // 1 - u_a having the complemented bits
-            const float la = (r.x & 0x80000000u) ? log1pf(-u01_f32(~r.x, ~r.y)) : logf(u01_f32(r.x, r.y));
+            // ln(u_a), the same for every lane (no divergent pair of library
+            // logarithms): u_a < 1/2 iff the top bit of r.x is clear, and then
+            // __logf (at most 3 ulp off [0.5, 2], 2^-21.41 absolute on it);
+            // above 1/2, with v = 1 - u_a from the complemented bits,
+            // ln(1 - v) = 2 atanh(s), s = -v / (2 - v), |s| < 1/3, by the odd
+            // Taylor series of atanh to s^15 (truncation below 2e-9 relative)
+            const float v = u01_f32(~r.x, ~r.y);
+            const float s = __fdividef(-v, 2.0f - v), s2 = s * s;
+            float t = 1.0f / 15.0f;
+            t = fmaf(t, s2, 1.0f / 13.0f);
+            t = fmaf(t, s2, 1.0f / 11.0f);
+            t = fmaf(t, s2, 1.0f / 9.0f);
+            t = fmaf(t, s2, 1.0f / 7.0f);
+            t = fmaf(t, s2, 1.0f / 5.0f);
+            t = fmaf(t, s2, 1.0f / 3.0f);
+            t = fmaf(t, s2, 1.0f);
+            const float la = (r.x & 0x80000000u) ? 2.0f * s * t : __logf(u01_f32(r.x, r.y));
             const float rho = sqrtf(-2.0f * la);
             float sn, cs;
             sincospif(2.0f * u01_f32(r.z, r.w), &sn, &cs);
