@@ -318,6 +318,14 @@ qr_status qr_sample(int d, const qr_nu* nu, unsigned long long seed, int instanc
                     long long m0, long long n, int j, int precision, double* u_out,
                     double* x_out, double* z_out);
 
+/* The d normals of Euler step j for paths m0 .. m0+n-1 of row i exactly as
+ * the FP32 compile-time tree path kernels and the shared-point group kernel
+ * draw them (Box-Muller on the same Philox words as qr_sample, Sec. 5
+ * sampling; their own FP32 logarithm), widened to double: z_out is a host
+ * array of n*d values. QR_EINVAL for d outside 1..8 or a NULL z_out. */
+qr_status qr_sample_normals_tree(int d, unsigned long long seed, int instance, int i, long long m0, long long n,
+                                 int j, double* z_out);
+
 /* ---- projection without device allocation -----------------------------
  * The paper has no counterpart to this call; it exists for callers that
  * cannot allocate device memory when they run it: code that owns a fixed

@@ -25,7 +25,7 @@ QR_HOST, QR_DEVICE = 0, 1
 EXPORTS = [
     "qr_init", "qr_picard_step", "qr_backward_sweep", "qr_eval", "qr_gamma_size", "qr_gamma_list",
     "qr_get_coefs", "qr_set_coefs", "qr_get_responses", "qr_set_profiling", "qr_get_stats",
-    "qr_last_error", "qr_status_string", "qr_destroy", "qr_philox_words", "qr_sample", "qr_project_static", "qr_test_points",
+    "qr_last_error", "qr_status_string", "qr_destroy", "qr_philox_words", "qr_sample", "qr_sample_normals_tree", "qr_project_static", "qr_test_points",
     "qr_selftest_wait_timeout",
     "qr_mlp_create", "qr_mlp_num_params", "qr_mlp_get_params", "qr_mlp_set_params", "qr_mlp_forward",
     "qr_mlp_gradients", "qr_mlp_train_step", "qr_mlp_last_error", "qr_mlp_destroy",
@@ -129,6 +129,9 @@ def load(path: str | None = None):
     L.qr_sample.restype = C.c_int
     L.qr_sample.argtypes = [C.c_int, C.POINTER(QrNu), C.c_ulonglong, C.c_int, C.c_int, C.c_longlong, C.c_longlong,
                             C.c_int, C.c_int, dp, dp, dp]
+    L.qr_sample_normals_tree.restype = C.c_int
+    L.qr_sample_normals_tree.argtypes = [C.c_int, C.c_ulonglong, C.c_int, C.c_int, C.c_longlong, C.c_longlong,
+                                         C.c_int, dp]
     fp = C.POINTER(C.c_float)
     L.qr_mlp_create.restype = C.c_int
     L.qr_mlp_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_ulonglong, vp]

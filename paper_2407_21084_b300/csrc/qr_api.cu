@@ -1172,6 +1172,28 @@ qr_status qr_sample(int d, const qr_nu* nu, unsigned long long seed, int instanc
     return s;
 }
 
+qr_status qr_sample_normals_tree(int d, unsigned long long seed, int instance, int i, long long m0, long long n,
+                                 int j, double* z_out)
+{
+    if (d < 1 || d > kDMax || !z_out || n < 0 || m0 < 0 || i < 0 || i >= 65536 || instance < 0 || instance >= 4096)
+        return QR_EINVAL;
+    if (n == 0) return QR_OK;
+    QrParams P{};
+    P.d = d;
+    P.key0 = (uint32_t)(seed & 0xffffffffull);
+    P.key1 = (uint32_t)(seed >> 32);
+    P.instance = instance;
+    double* buf = nullptr;
+    const size_t bytes = sizeof(double) * (size_t)n * d;
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) return QR_ENOMEM;
+    qr_status s = QR_OK;
+    if (launch_normals_tree(P, i, m0, n, j, buf, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(z_out, buf, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        s = QR_ECUDA;
+    cudaFree(buf);
+    return s;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------------ batches

@@ -91,4 +91,33 @@ cudaError_t launch_pack_tree(int prec, const double2* alpha, int nG, const TreeM
     return cudaGetLastError();
 }
 
+// the Box-Muller normals of Euler step j exactly as the FP32 tree path kernels
+// draw them (normals_fast), widened to double: z is n rows of d values
+template <int D>
+__global__ void k_normals_tree(const __grid_constant__ QrParams P, int i, long long m0, long long n, int j,
+                               double* __restrict__ z)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    float zz[D];
+    normals_fast<float, D>(P, i, (uint32_t)(m0 + t), j, zz);
+#pragma unroll
+    for (int l = 0; l < D; ++l) z[t * D + l] = (double)zz[l];
+}
+
+cudaError_t launch_normals_tree(const QrParams& P, int i, long long m0, long long n, int j, double* z,
+                                cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    switch (P.d) {
+#define QR_X(DD) \
+    case DD: k_normals_tree<DD><<<blocks, 128, 0, st>>>(P, i, m0, n, j, z); break;
+        QR_X(1) QR_X(2) QR_X(3) QR_X(4) QR_X(5) QR_X(6) QR_X(7) QR_X(8)
+#undef QR_X
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+
 }  // namespace qr

@@ -95,6 +95,8 @@ cudaError_t launch_test_points(const QrParams& P, int i, long long n, double* x,
 cudaError_t launch_philox(const uint32_t* ctr_key, long long n, uint32_t* out, cudaStream_t st);
 cudaError_t launch_sample(int prec, const QrParams& P, int i, long long m0, long long n, int j,
                           double* u, double* x, double* z, cudaStream_t st);
+cudaError_t launch_normals_tree(const QrParams& P, int i, long long m0, long long n, int j, double* z,
+                                cudaStream_t st);
 
 // read-only view of a context's device problem description (qr_api.cu)
 struct CtxView {

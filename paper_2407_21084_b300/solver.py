@@ -188,6 +188,14 @@ def philox_words(ctr_key: np.ndarray) -> np.ndarray:
     return out
 
 
+def sample_normals_tree(d, seed, instance, i, m0, n, j):
+    """FP32 normals of the tree path kernels, shape (n, d)."""
+    lib = L.load()
+    z = np.zeros((n, d))
+    L.check(lib.qr_sample_normals_tree(d, seed, instance, i, m0, n, j, _dp(z)))
+    return z
+
+
 def sample(d, nu_kind, mu, seed, instance, i, m0, n, j, precision=L.QR_FP64):
     """Device sampler: (u, x, z) arrays of shape (n, d)."""
     lib = L.load()

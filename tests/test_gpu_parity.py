@@ -68,6 +68,18 @@ def test_sampler(qr, ora, prec):
         assert np.all(np.abs(z[t] - zo) <= tol * (1 + np.abs(zo)))
 
 
+@pytest.mark.parametrize("d", [1, 5, 6, 8])
+def test_tree_kernel_normals(qr, ora, d):
+    """The normals the FP32 tree path kernels draw (their own branch-free
+    Box-Muller logarithm) against the oracle's, at the FP32 sampler bound,
+    on both sides of u = 1/2 and deep in the tails (many paths)."""
+    seed, inst, i, m0, n, j = 0x5EED0F7EE, 2, 7, 12345, 20000, 3
+    z = qr.sample_normals_tree(d, seed, inst, i, m0, n, j)
+    for t in range(0, n, 7):
+        zo = ora.normals(seed, inst, i, m0 + t, j, d)
+        assert np.all(np.abs(z[t] - zo) <= 3e-6 * (1 + np.abs(zo))), (t, z[t], zo)
+
+
 # ------------------------------------------------------------- iteration
 def _solver(qr, w, prec, M=None, clamp=True, kern=0):
     return qr.Solver.from_workload(w, precision=prec, M=M, clamp=clamp, path_kernel=kern)
