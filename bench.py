@@ -31,11 +31,37 @@ sys.path.insert(0, ROOT)
 from paper_2407_21084_b300 import workloads as W  # noqa: E402
 
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-SMS, FP32_LANES = 148, 128  # B300 SMs, FP32 FMA lanes per SM per clock
 
 
-def fp32_peak_tflops(clock_mhz: float) -> float:
-    return SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
+def cpu_model() -> str:
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def measure_peaks(dev: int, stream) -> dict:
+    """FMA throughput of this device's FP32 and FP64 pipes, measured in
+    process by the library's FMA-chain kernels (qr_fma_peak): a burst of
+    about 60 ms and a run of about 2 s per kind, with the SM clocks sampled
+    meanwhile. The FP32 peak is the larger of the scalar and the packed
+    two-lane form."""
+    from paper_2407_21084_b300 import _lib as L
+
+    out = {}
+    with ClockSampler(dev) as clk:
+        for name, kind in (("fp32", L.QR_PEAK_FP32), ("fp32x2", L.QR_PEAK_FP32X2), ("fp64", L.QR_PEAK_FP64)):
+            b = L.fma_peak(kind, 60.0, stream.cuda_stream)
+            su = L.fma_peak(kind, 2000.0, stream.cuda_stream)
+            out[name] = {"burst_tflops": b["tflops"], "sustained_tflops": su["tflops"], "sustained_ms": su["ms"]}
+            out["sm_count"] = su["sm_count"]
+    out["clocks"] = clk.summary()
+    out["how"] = ("qr_fma_peak: resident 256-thread CTAs on every SM, 8 independent FMA chains per thread, "
+                  "~20 ms launches timed with CUDA events: ~60 ms (burst) and ~2 s (sustained) per kind")
+    return out
 
 
 class ClockSampler:
@@ -139,6 +165,7 @@ def cpu_baseline(w: W.Workload, alpha_prev: np.ndarray, rows, m_sample: int, gpu
     dt = time.perf_counter() - t0
     cores = min(oracle.max_threads(), -(-m_sample // 1024))  # one chunk of >= 1024 paths per thread
     base = {"value": evals / dt, "unit": "path.coef evals/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(), "host_threads": os.cpu_count(),
             "sample": "rows i=%s of one Picard iteration, first %d of %d paths, FP64 oracle (OpenMP), %.1f s"
                       % (list(rows), m_sample, w.M, dt)}
     return base, ref, p
@@ -211,6 +238,7 @@ def main():
                       solver.L.QR_F_CUBIC_MANUF, w.f_par, solver.L.QR_GT_COS, w.g_par, w.M, w.seed,
                       precision=prec, clamp_L=w.clamp_L, instance=rank, stream=stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (126 MB)
+    peaks = measure_peaks(dev, stream)
 
     for _ in range(args.warmup):
         s.picard_step(1)
@@ -261,7 +289,12 @@ def main():
     series_points = w.M * w.N * (w.N - 1) / 2.0
     flops_paths = series_points * pairs * 8.0  # 4 FP32 FMA per pair (complex Horner step)
     clocks = clk.summary()
-    peak = fp32_peak_tflops(clocks["sm_max_mhz"] or 2032.0)
+    # roofline denominator: the FP32 FMA rate measured on this device, the
+    # sustained figure (the path kernel runs ~0.8 s launches back to back
+    # inside a long timed region), the larger of scalar and packed FMA
+    pk = peaks
+    peak = max(pk["fp32"]["sustained_tflops"], pk["fp32x2"]["sustained_tflops"])
+    peak_burst = max(pk["fp32"]["burst_tflops"], pk["fp32x2"]["burst_tflops"])
     achieved = flops_paths / (ms_paths / 1e3) / 1e12
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic_paths_c3.json")
@@ -278,6 +311,7 @@ def main():
     e2e_ms = []
     a_host = s.coefs()
     for _ in range(args.steps):
+        flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s.set_coefs(a_host)
@@ -297,12 +331,16 @@ def main():
         "kernels_ms": {"paths": ms_paths, "project": ms_proj, "reduce": ms_red},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_paths (path-and-series)",
-                     "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived; no FP32 peak in "
-                                   "MEASURED_PEAKS.json)",
-                     "work": "M N(N-1)/2 series points x (|Gamma|+1)/2 pairs x 8 flop",
-                     "peak_at_measured_clock": fp32_peak_tflops(clocks["sm_mhz"] or 2032.0),
-                     "frac_at_measured_clock": achieved / fp32_peak_tflops(clocks["sm_mhz"] or 2032.0)},
+                     "kernel": "k_paths_tree (path-and-series)",
+                     "peak_basis": "measured FP32 FMA rate of this device, sustained (~2 s of FMA chains, "
+                                   "qr_fma_peak), max of scalar and packed two-lane FMA; of measured",
+                     "peak_burst": peak_burst, "frac_of_burst": achieved / peak_burst,
+                     "work": "M N(N-1)/2 series points x (|Gamma|+1)/2 pairs x 8 flop"},
+        "fp32_peak_measured": {"sustained_tflops": peak, "burst_tflops": peak_burst,
+                               "scalar": pk["fp32"], "packed_x2": pk["fp32x2"]},
+        "fp64_peak_measured": pk["fp64"],
+        "sm_count": pk["sm_count"],
+        "peak_clocks": pk["clocks"],
         "clocks": clocks,
         "gpu_launches": 4 * args.steps,  # per iteration: path, projection, reduction, tree repack
         "e2e": {"value": e2e_val, "unit": "path.coef evals/s", "h2d_bytes_per_step": io_bytes,

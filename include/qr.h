@@ -326,6 +326,25 @@ qr_status qr_sample(int d, const qr_nu* nu, unsigned long long seed, int instanc
 qr_status qr_sample_normals_tree(int d, unsigned long long seed, int instance, int i, long long m0, long long n,
                                  int j, double* z_out);
 
+/* ---- arithmetic peaks of this device (the paper has no counterpart) -----
+ * The denominators of the rooflines the benchmark reports: the rate at which
+ * the SMs of the current device retire fused multiply-adds, measured, not
+ * derived from a lane count and a clock. A grid that fills every SM
+ * (resident 256-thread CTAs x multiprocessors) runs 8 independent FMA chains
+ * per thread, in launches of about 20 ms repeated for about `ms`
+ * milliseconds (a few tens of ms: the burst rate; seconds: the rate the
+ * power and thermal limits sustain), timed with CUDA events on `stream`
+ * (cudaStream_t, NULL = default stream). No device setting is touched.
+ *   kind:        QR_PEAK_FP32 (scalar FP32 FMA), QR_PEAK_FP32X2 (packed
+ *                two-lane FP32 FMA, counted as two), QR_PEAK_FP64.
+ *   tflops_out:  2 flop per FMA / elapsed time, in TFLOP/s (host, nullable).
+ *   ms_out:      elapsed device time of the timed launches (host, nullable).
+ *   sm_count_out: multiprocessors of the current device (host, nullable).
+ * Allocates a small result buffer on the stream (one value per thread).
+ * Blocks until done. QR_EINVAL for an unknown kind or ms outside (0, 60000]. */
+enum { QR_PEAK_FP32 = 0, QR_PEAK_FP32X2 = 1, QR_PEAK_FP64 = 2 };
+qr_status qr_fma_peak(int kind, double ms, void* stream, double* tflops_out, double* ms_out, int* sm_count_out);
+
 /* ---- projection without device allocation -----------------------------
  * The paper has no counterpart to this call; it exists for callers that
  * cannot allocate device memory when they run it: code that owns a fixed
@@ -339,8 +358,11 @@ qr_status qr_sample_normals_tree(int d, unsigned long long seed, int instance, i
  *
  * Computes coefficient rows i in [i_lo, i_hi) from responses S given by the
  * caller: alpha_{i,k} = (1/M) sum_m S_i^m conj(phi_k(U_i^m)), with the start
- * uniforms U regenerated from the context's seed, exactly as the projection
- * inside qr_picard_step does.
+ * uniforms U regenerated from the context's seed, by the same kernel the
+ * projection inside qr_picard_step runs for this context (the compiled tiled
+ * projection when one covers the index set, else the table-driven one).
+ * The work runs on the context's device, which the call makes current for
+ * its duration (the caller's current device is restored).
  *   S:         device array, (i_hi - i_lo) rows of M responses, row-major, in
  *              the context's precision (float for QR_FP32, double for QR_FP64).
  *   alpha_out: device array, (i_hi - i_lo) rows of |Gamma| complex values as

@@ -20,6 +20,7 @@ QR_GT_COS, QR_GT_TRIGPOLY, QR_GT_PAPER_SIN = range(3)
 QR_FP64, QR_FP32 = 0, 1
 QR_U_PHILOX, QR_U_LATTICE = 0, 1
 QR_HOST, QR_DEVICE = 0, 1
+QR_PEAK_FP32, QR_PEAK_FP32X2, QR_PEAK_FP64 = range(3)
 
 # every symbol declared in include/qr.h
 EXPORTS = [
@@ -30,7 +31,7 @@ EXPORTS = [
     "qr_mlp_create", "qr_mlp_num_params", "qr_mlp_get_params", "qr_mlp_set_params", "qr_mlp_forward",
     "qr_mlp_gradients", "qr_mlp_train_step", "qr_mlp_last_error", "qr_mlp_destroy",
     "qr_batch_create", "qr_batch_picard_step", "qr_batch_info", "qr_batch_set_grouping", "qr_batch_groups",
-    "qr_batch_last_error", "qr_batch_destroy",
+    "qr_batch_last_error", "qr_batch_destroy", "qr_fma_peak",
 ]
 
 
@@ -171,6 +172,8 @@ def load(path: str | None = None):
     L.qr_test_points.argtypes = [vp, C.c_int, C.c_longlong, dp]
     L.qr_project_static.restype = C.c_int
     L.qr_project_static.argtypes = [vp, vp, C.c_int, C.c_int, vp]
+    L.qr_fma_peak.restype = C.c_int
+    L.qr_fma_peak.argtypes = [C.c_int, C.c_double, vp, dp, dp, C.POINTER(C.c_int)]
     _lib = L
     return L
 
@@ -180,3 +183,12 @@ def check(status: int, ctx=None):
         L = load()
         msg = L.qr_last_error(ctx).decode() if ctx else L.qr_status_string(status).decode()
         raise QrError(status, msg or L.qr_status_string(status).decode())
+
+
+def fma_peak(kind: int, ms: float, stream: int | None = None) -> dict:
+    """Measured FMA throughput of the current device (qr_fma_peak):
+    {"tflops", "ms", "sm_count"}."""
+    L = load()
+    tf, el, sms = C.c_double(), C.c_double(), C.c_int()
+    check(L.qr_fma_peak(kind, ms, C.c_void_p(stream or 0), C.byref(tf), C.byref(el), C.byref(sms)))
+    return {"tflops": tf.value, "ms": el.value, "sm_count": sms.value}

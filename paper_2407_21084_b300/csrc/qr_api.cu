@@ -425,6 +425,11 @@ bool ctx_view(const qr_ctx* c, CtxView* v)
     v->tab = c->d_tab;
     v->first = c->d_first;
     v->stream = c->stream;
+    v->device = c->device;
+    v->proj_nodes = c->proj_nodes;
+    v->gkind = c->gkind;
+    v->gn = c->gn;
+    v->perm = c->d_perm;
     return true;
 }
 void ctx_set_error(qr_ctx* c, const char* msg)

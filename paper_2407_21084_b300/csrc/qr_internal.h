@@ -105,6 +105,10 @@ struct CtxView {
     const GEntry* tab;
     const uint8_t* first;
     cudaStream_t stream;
+    int device;      // the device the context's buffers and stream live on
+    int proj_nodes;  // nonzero: a compiled tiled projection covers the index set
+    int gkind, gn;   // its index-set kind and level
+    const int* perm; // its slot -> canonical half-set order
 };
 }  // namespace qr
 

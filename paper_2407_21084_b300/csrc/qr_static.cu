@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <mutex>
 
+#include "qr_fast.h"
 #include "qr_internal.h"
 
 namespace {
@@ -23,17 +24,24 @@ static __device__ __align__(256) double2 g_partials[kPartialSlots];
 std::mutex g_mu;
 double2* g_addr[kMaxDevices] = {};
 
-// device address of g_partials on the current device, looked up once per device
-cudaError_t scratch_address(double2** out)
+// device address of g_partials on device `dev` (the context's device),
+// looked up once per device with that device current; the caller's current
+// device is restored afterwards
+cudaError_t scratch_address(int dev, double2** out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_addr[dev]) {
+        int cur = 0;
+        cudaError_t e = cudaGetDevice(&cur);
+        if (e != cudaSuccess) return e;
+        if (cur != dev && (e = cudaSetDevice(dev)) != cudaSuccess) return e;
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_partials);
+        if (cur != dev) {
+            const cudaError_t e2 = cudaSetDevice(cur);
+            if (e == cudaSuccess) e = e2;
+        }
         if (e != cudaSuccess) return e;
         g_addr[dev] = static_cast<double2*>(p);
     }
@@ -87,10 +95,31 @@ extern "C" qr_status qr_project_static(qr_ctx* ctx, const void* S, int i_lo, int
         qr::ctx_set_error(ctx, msg);
         return QR_EINVAL;
     }
+    // the context's device is current for the call (its stream and buffers
+    // live there); the caller's current device is restored on return
+    int cur = 0;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e == cudaSuccess && cur != v.device) e = cudaSetDevice(v.device);
+    if (e != cudaSuccess) {
+        qr::ctx_set_error(ctx, cudaGetErrorString(e));
+        return QR_ECUDA;
+    }
+    struct Restore {
+        int dev;
+        bool on;
+        ~Restore()
+        {
+            if (on) (void)cudaSetDevice(dev);
+        }
+    } restore{cur, cur != v.device};
     double2* scratch = nullptr;
-    cudaError_t e = scratch_address(&scratch);
+    e = scratch_address(v.device, &scratch);
+    // the same projection kernel qr_picard_step runs for this context: the
+    // compiled tiled projection when one covers the index set, else the
+    // table-driven one; both write every partial slot of the rows they cover
     if (e == cudaSuccess)
-        e = qr::launch_project(v.prec, P, v.tab, v.first, S, scratch, i_lo, i_hi, v.stream);
+        e = v.proj_nodes ? qr::launch_project_tree(v.prec, v.gkind, v.gn, P, S, v.perm, scratch, i_lo, i_hi, v.stream)
+                         : qr::launch_project(v.prec, P, v.tab, v.first, S, scratch, i_lo, i_hi, v.stream);
     if (e == cudaSuccess) {
         const long long total = (long long)(i_hi - i_lo) * P.nGp;
         k_reduce_rows<<<(unsigned)((total + 255) / 256), 256, 0, v.stream>>>(

@@ -7,6 +7,18 @@
 #include "qr_device.cuh"
 #include "qr_fast.h"
 
+// FP32 per-step transcendentals (see nu_phase_fast, rcos_fast and
+// normals_fast below): SFU forms on exactly reduced arguments
+#ifndef QR_FAST_PHASE
+#define QR_FAST_PHASE 1
+#endif
+#ifndef QR_FAST_BM
+#define QR_FAST_BM 0
+#endif
+#ifndef QR_FAST_FCOS
+#define QR_FAST_FCOS 1
+#endif
+
 namespace qr {
 
 template <int D, int NN, int KIND>
@@ -110,11 +122,66 @@ __device__ __forceinline__ void normals_fast(const QrParams& P, int i, uint32_t 
             const float la = (r.x & 0x80000000u) ? 2.0f * s * t : __logf(u01_f32(r.x, r.y));
             const float rho = sqrtf(-2.0f * la);
             float sn, cs;
+#if QR_FAST_BM
+            // (cos, sin)(2 pi u_b) = -(cos, sin)(2 pi (u_b - 1/2)), argument in [-pi, pi]
+            __sincosf(6.28318530717958648f * (u01_f32(r.z, r.w) - 0.5f), &sn, &cs);
+            sn = -sn;
+            cs = -cs;
+#else
             sincospif(2.0f * u01_f32(r.z, r.w), &sn, &cs);
+#endif
             z[2 * c] = rho * cs;
             if (2 * c + 1 < D) z[2 * c + 1] = rho * sn;
         }
     }
+}
+
+// ---- FP32 per-step transcendentals of the tree path kernels
+// The phases e^{2 pi i F(x)} of the series and the cosine of the driver are
+// evaluated with the SFU's sine/cosine (__sincosf, __cosf: absolute error at
+// most 2^-21.41 on [-pi, pi]) on arguments reduced to that range exactly:
+//  * phase: with w = F(-|x|) = (1/2)(1+|x|)^-3 in (0, 1/2] (double Lomax,
+//    mu = 3), the angle 2 pi w lies in (0, pi] with no reduction, and
+//    e^{2 pi i F(x)} = e^{-+2 pi i w} for x >= 0 / x < 0; the reciprocal is
+//    the SFU's (__fdividef, 2 ulp);
+//  * cosine of an argument a: Cody-Waite reduction r = a - 2 pi rint(a/2pi)
+//    with 2 pi split into a float and its float remainder, each product
+//    exact inside an FMA, so |r| <= pi + 1e-6 for |a| < 2^20; larger |a|
+//    (far tails of the start law) take the library cosf.
+
+template <typename R>
+__device__ __forceinline__ V2<R> nu_phase_fast(const QrParams& P, R x)
+{
+#if QR_FAST_PHASE
+    if constexpr (sizeof(R) == 4) {
+        if (P.nu_kind == QR_NU_LOMAX && P.mu_is3 && !P.half_angle) {
+            const float ax = fabsf(x);
+            const float r = __fdividef(1.0f, 1.0f + ax);
+            const float w = 0.5f * r * r * r;
+            float sn, cs;
+            __sincosf(6.28318530717958648f * w, &sn, &cs);
+            return make_float2(cs, x < 0.0f ? sn : -sn);
+        }
+    }
+#endif
+    return nu_phase<R>(P, x);
+}
+
+template <typename R>
+__device__ __forceinline__ R rcos_fast(R a)
+{
+#if QR_FAST_FCOS
+    if constexpr (sizeof(R) == 4) {
+        if (fabsf(a) < 1048576.0f) {
+            const float k = rintf(a * 0.159154943091895336f);
+            float r = fmaf(-k, 6.28318548202514648f, a);  // float(2 pi)
+            r = fmaf(-k, -1.74845553146951715e-7f, r);    // 2 pi - float(2 pi)
+            return __cosf(r);
+        }
+        return cosf(a);
+    }
+#endif
+    return rcos<R>(a);
 }
 
 template <typename R, int D>
@@ -144,7 +211,7 @@ __device__ __forceinline__ R drv_f_fast(const QrParams& P, const StepConsts<R, D
         R sx = 0;
 #pragma unroll
         for (int l = 0; l < D; ++l) sx += K.fs[l] * x[l];
-        const R u = fexp_j * rcos<R>(sx);
+        const R u = fexp_j * rcos_fast<R>(sx);
         return -y * y * y + (K.fc * u + u * u * u);
     }
     case QR_F_PAPER_MIN: {
@@ -167,7 +234,7 @@ __device__ __forceinline__ R term_g_fast(const QrParams& P, const StepConsts<R, 
     if (P.g_kind == QR_GT_COS) {
 #pragma unroll
         for (int l = 0; l < D; ++l) sx += K.gs[l] * x[l];
-        return rcos<R>(sx);
+        return rcos_fast<R>(sx);
     }
 #pragma unroll
     for (int l = 0; l < D; ++l) sx += x[l];
@@ -415,7 +482,7 @@ __device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __res
 #pragma unroll
             for (int p = 0; p < P; ++p)
 #pragma unroll
-                for (int l = 0; l < D; ++l) zz[p][l] = nu_phase<R>(Pm, x1[p][l]);
+                for (int l = 0; l < D; ++l) zz[p][l] = nu_phase_fast<R>(Pm, x1[p][l]);
             tree_series<R, D, NN, KIND, P>(abuf[buf], zz, y);
             if (K.damp && row < N) {
 #pragma unroll

@@ -230,3 +230,81 @@ def test_manufactured_cubic_approaches_projection_of_exact_solution(ora):
     assert e_big[-1] < 0.05
     assert e_small[-1] / e_big[-1] > 2.5  # sqrt(16) = 4 in the pure-variance regime
     assert e_big.max() < 0.12
+
+
+def _lattice_recursion(Phi, gvals, N, lam, L, n_iter, where="y_next"):
+    """The Jacobi-Picard iteration of Algorithm 1 written out in numpy for
+    paths that stand still (sigma = 0, b = 0, start points on the centred
+    lattice), f = lam*y: S_i = g + lam dt sum_{j=i}^{N-1} y_{j+1} with
+    y_N = g and, for j+1 < N, y_{j+1} = T_L(ybar_{j+1}) (eq. Sqi:bar:M with
+    the truncation of eq. TL:2); alpha_i = Phi^H S_i / M (eq. Aqi:bar:M);
+    ybar_i = Re Phi alpha_i. `where` moves the truncation elsewhere (to
+    show that the pin tells the placements apart): "none", "g" (also on
+    y_N), "f" (on lam*y instead of y), "S" (on the response)."""
+    M = Phi.shape[0]
+    dt = 1.0 / N
+    alpha = np.zeros((N, Phi.shape[1]), dtype=complex)
+    hits = 0
+
+    def clamp(v):
+        return np.clip(v, -L, L)
+
+    for _ in range(n_iter):
+        ybar = (Phi @ alpha.T).real  # M x N: ybar_j at the lattice points
+        new = np.empty_like(alpha)
+        for i in range(N):
+            S = gvals.copy() if where != "g" else clamp(gvals)
+            for j in range(i, N):
+                if j + 1 == N:
+                    y1 = clamp(gvals) if where == "g" else gvals
+                else:
+                    y1 = ybar[:, j + 1]
+                    if where == "y_next":
+                        hits += int(np.count_nonzero(np.abs(y1) > L))
+                        y1 = clamp(y1)
+                term = lam * y1
+                if where == "f" and j + 1 < N:
+                    term = clamp(term)
+                S = S + term * dt
+            if where == "S":
+                S = clamp(S)
+            new[i] = Phi.conj().T @ S / M
+        alpha = new
+    return alpha, hits
+
+
+def _clamp_case(ora):
+    d, kind, n, lat, N, lam = 2, 0, 2, 5, 4, 0.7
+    K = ora.gamma_list(kind, d, n)
+    c = _planted_coefs(np.random.default_rng(31), K)
+    c *= 0.25
+    p = _lattice_problem(ora, d, kind, n, lat, N, ora.F_LINEAR, [lam], c)
+    # lattice points in the oracle's order (dimension 0 = least significant digit)
+    m = np.arange(lat ** d)
+    U = np.stack([((m // lat ** l) % lat + 0.5) / lat for l in range(d)], axis=1)
+    Phi = np.exp(2j * np.pi * (U @ K.T))
+    gvals = (Phi @ c).real
+    L = 0.6 * np.abs(gvals).max()  # below max|y|: the truncation binds
+    p.clamp_L = L
+    return p, Phi, gvals, N, lam, L
+
+
+def test_truncation_TL_placement_on_lattice(ora):
+    """T_L of eq. (TL:2) applied where eq. (Sqi:bar:M) puts it: to the
+    previous iterate's series ybar_{j+1}(X_{j+1}) before the driver, not to
+    g = y_N, not to f's output, not to the response. With standing paths on
+    a lattice the whole scheme is a few numpy products, so the oracle's
+    clamped Picard iterates are fixed independently, and the clamp count is
+    the number of series values beyond L."""
+    p, Phi, gvals, N, lam, L = _clamp_case(ora)
+    for q in (1, 2, N):
+        ref, hits_ref = _lattice_recursion(Phi, gvals, N, lam, L, q)
+        a, hits = ora.picard(p, q)
+        scale = np.abs(ref).max()
+        assert np.abs(a - ref).max() < 1e-12 * scale
+        assert hits == hits_ref
+    assert hits_ref > 0
+    # every other placement gives a visibly different fixed point
+    for where in ("none", "g", "f", "S"):
+        alt, _ = _lattice_recursion(Phi, gvals, N, lam, L, N, where=where)
+        assert np.abs(alt - ref).max() > 1e-3 * scale, where
