@@ -48,12 +48,13 @@ def measure_peaks(dev: int, stream) -> dict:
     process by the library's FMA-chain kernels (qr_fma_peak): a burst of
     about 60 ms and a run of about 2 s per kind, with the SM clocks sampled
     meanwhile. The FP32 peak is the larger of the scalar and the packed
-    two-lane form."""
+    two-lane form and of the two interleaved."""
     from paper_2407_21084_b300 import _lib as L
 
     out = {}
     with ClockSampler(dev) as clk:
-        for name, kind in (("fp32", L.QR_PEAK_FP32), ("fp32x2", L.QR_PEAK_FP32X2), ("fp64", L.QR_PEAK_FP64)):
+        for name, kind in (("fp32", L.QR_PEAK_FP32), ("fp32x2", L.QR_PEAK_FP32X2),
+                           ("fp32mix", L.QR_PEAK_FP32MIX), ("fp64", L.QR_PEAK_FP64)):
             b = L.fma_peak(kind, 60.0, stream.cuda_stream)
             su = L.fma_peak(kind, 2000.0, stream.cuda_stream)
             out[name] = {"burst_tflops": b["tflops"], "sustained_tflops": su["tflops"], "sustained_ms": su["ms"]}
@@ -171,6 +172,68 @@ def cpu_baseline(w: W.Workload, alpha_prev: np.ndarray, rows, m_sample: int, gpu
     return base, ref, p
 
 
+def bench_c4(stream, steps: int, flush) -> dict:
+    """The many-instance workload: 256 problems of uneven d, |Gamma| and N
+    (M = 2^18 each, 64 of them sharing their sample points) advanced by one
+    batched Picard iteration per step (persistent path kernel, tensor-core
+    shared-point kernel, projections). Device time with CUDA events on the
+    batch's stream (L2 flushed before each step; the batch's state, ~10 GB,
+    is far larger than L2 anyway), and end to end through the C-ABI with
+    every instance's coefficients copied from and back to host memory."""
+    import torch
+
+    from paper_2407_21084_b300 import batch as B
+
+    ws_ = W.c4()
+    t0 = time.perf_counter()
+    sol = B.solvers_for(ws_, stream.cuda_stream)
+    b = B.Batch(sol)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b.picard_step(1)  # autotuning of tiles and grid, then the first iteration
+    t_tune = time.perf_counter() - t0
+    b.picard_step(1)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.picard_step(1)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    evals = sum(w.evals_per_iter() for w in ws_)
+    host = [s.coefs() for s in sol]
+    io = sum(a.nbytes for a in host)
+    e2e = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s, a in zip(sol, host):
+            s.set_coefs(a)
+        b.picard_step(1)
+        host = [s.coefs() for s in sol]
+        e2e.append(time.perf_counter() - t0)
+    info = b.info()
+    b.close()
+    for s in sol:
+        s.close()
+    ms_step = float(np.mean(ms))
+    return {"workload": "c4_256_instances_M262144", "instances": len(ws_),
+            "shared_point_instances": info["grouped_instances"], "shared_groups": info["shared_groups"],
+            "dims": sorted(set(w.d for w in ws_)),
+            "n_gamma_range": [min(w.n_gamma() for w in ws_), max(w.n_gamma() for w in ws_)],
+            "evals_per_iteration": evals, "s_per_batch_iteration": ms_step / 1e3,
+            "path_coef_evals_per_s": evals / (ms_step / 1e3), "steps": steps,
+            "autotune": {"tiles_per_item": info["tiles_per_item"], "grid": info["grid"], "s": t_tune},
+            "setup_s": t_setup,
+            "e2e": {"value": evals / float(np.mean(e2e)), "unit": "path.coef evals/s",
+                    "h2d_bytes_per_step": io, "d2h_bytes_per_step": io}}
+
+
 def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -210,6 +273,7 @@ def main():
     ap.add_argument("--ref-paths", type=int, default=98304, help="paths of the oracle sample (10-25 s on 8-16 cores)")
     ap.add_argument("--paths", type=int, default=0, help="override M (profiling captures only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c4", action="store_true", help="skip the many-instance (config 4) key")
     args = ap.parse_args()
     w = W.CONFIGS[args.workload]()
     if args.paths:
@@ -293,8 +357,9 @@ def main():
     # sustained figure (the path kernel runs ~0.8 s launches back to back
     # inside a long timed region), the larger of scalar and packed FMA
     pk = peaks
-    peak = max(pk["fp32"]["sustained_tflops"], pk["fp32x2"]["sustained_tflops"])
-    peak_burst = max(pk["fp32"]["burst_tflops"], pk["fp32x2"]["burst_tflops"])
+    fp32_forms = ("fp32", "fp32x2", "fp32mix")
+    peak = max(pk[f]["sustained_tflops"] for f in fp32_forms)
+    peak_burst = max(pk[f]["burst_tflops"] for f in fp32_forms)
     achieved = flops_paths / (ms_paths / 1e3) / 1e12
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic_paths_c3.json")
@@ -333,11 +398,11 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_paths_tree (path-and-series)",
                      "peak_basis": "measured FP32 FMA rate of this device, sustained (~2 s of FMA chains, "
-                                   "qr_fma_peak), max of scalar and packed two-lane FMA; of measured",
+                                   "qr_fma_peak), max of scalar, packed two-lane and interleaved FMA; of measured",
                      "peak_burst": peak_burst, "frac_of_burst": achieved / peak_burst,
                      "work": "M N(N-1)/2 series points x (|Gamma|+1)/2 pairs x 8 flop"},
         "fp32_peak_measured": {"sustained_tflops": peak, "burst_tflops": peak_burst,
-                               "scalar": pk["fp32"], "packed_x2": pk["fp32x2"]},
+                               "scalar": pk["fp32"], "packed_x2": pk["fp32x2"], "mixed": pk["fp32mix"]},
         "fp64_peak_measured": pk["fp64"],
         "sm_count": pk["sm_count"],
         "peak_clocks": pk["clocks"],
@@ -370,6 +435,8 @@ def main():
         g.close()
         line["sup_error_vs_fp64_oracle"] = {"value": sup, "test_points": w.n_test, "rows": rows,
                                             "paths": args.ref_paths}
+    if rank == 0 and ws == 1 and not args.no_c4:
+        line["c4_batch"] = bench_c4(stream, max(2, min(args.steps, 5)), flush)
     if rank == 0:
         print(json.dumps(line), flush=True)
     s.close()

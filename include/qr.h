@@ -326,6 +326,17 @@ qr_status qr_sample(int d, const qr_nu* nu, unsigned long long seed, int instanc
 qr_status qr_sample_normals_tree(int d, unsigned long long seed, int instance, int i, long long m0, long long n,
                                  int j, double* z_out);
 
+/* Test hook (the paper has no counterpart): one 128 x 32 x 64 product
+ * D = A B^T on the 5th-generation tensor cores (tcgen05.mma, BF16 operands
+ * staged in 128-byte swizzled shared memory, FP32 accumulator in tensor
+ * memory, read back by tcgen05.ld) -- the building block of the shared-point
+ * group kernel, checked against a product computed on the host.
+ *   A: 128 x 64 BF16 (raw 16-bit patterns), row-major, host.
+ *   B: 32 x 64 BF16, row-major, host.   D: 128 x 32 floats, row-major, host.
+ * QR_ETIMEOUT if the tensor core never signalled completion (bounded wait),
+ * QR_ECUDA on a CUDA error or misplaced tiles. Blocks until done. */
+qr_status qr_tc_selftest(const uint16_t* A, const uint16_t* B, float* D);
+
 /* ---- arithmetic peaks of this device (the paper has no counterpart) -----
  * The denominators of the rooflines the benchmark reports: the rate at which
  * the SMs of the current device retire fused multiply-adds, measured, not
@@ -336,13 +347,15 @@ qr_status qr_sample_normals_tree(int d, unsigned long long seed, int instance, i
  * power and thermal limits sustain), timed with CUDA events on `stream`
  * (cudaStream_t, NULL = default stream). No device setting is touched.
  *   kind:        QR_PEAK_FP32 (scalar FP32 FMA), QR_PEAK_FP32X2 (packed
- *                two-lane FP32 FMA, counted as two), QR_PEAK_FP64.
+ *                two-lane FP32 FMA, counted as two), QR_PEAK_FP64,
+ *                QR_PEAK_FP32MIX (half the chains scalar, half packed,
+ *                interleaved: both FP32 instruction forms in flight).
  *   tflops_out:  2 flop per FMA / elapsed time, in TFLOP/s (host, nullable).
  *   ms_out:      elapsed device time of the timed launches (host, nullable).
  *   sm_count_out: multiprocessors of the current device (host, nullable).
  * Allocates a small result buffer on the stream (one value per thread).
  * Blocks until done. QR_EINVAL for an unknown kind or ms outside (0, 60000]. */
-enum { QR_PEAK_FP32 = 0, QR_PEAK_FP32X2 = 1, QR_PEAK_FP64 = 2 };
+enum { QR_PEAK_FP32 = 0, QR_PEAK_FP32X2 = 1, QR_PEAK_FP64 = 2, QR_PEAK_FP32MIX = 3 };
 qr_status qr_fma_peak(int kind, double ms, void* stream, double* tflops_out, double* ms_out, int* sm_count_out);
 
 /* ---- projection without device allocation -----------------------------

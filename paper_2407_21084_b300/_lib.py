@@ -20,7 +20,7 @@ QR_GT_COS, QR_GT_TRIGPOLY, QR_GT_PAPER_SIN = range(3)
 QR_FP64, QR_FP32 = 0, 1
 QR_U_PHILOX, QR_U_LATTICE = 0, 1
 QR_HOST, QR_DEVICE = 0, 1
-QR_PEAK_FP32, QR_PEAK_FP32X2, QR_PEAK_FP64 = range(3)
+QR_PEAK_FP32, QR_PEAK_FP32X2, QR_PEAK_FP64, QR_PEAK_FP32MIX = range(4)
 
 # every symbol declared in include/qr.h
 EXPORTS = [
@@ -31,7 +31,7 @@ EXPORTS = [
     "qr_mlp_create", "qr_mlp_num_params", "qr_mlp_get_params", "qr_mlp_set_params", "qr_mlp_forward",
     "qr_mlp_gradients", "qr_mlp_train_step", "qr_mlp_last_error", "qr_mlp_destroy",
     "qr_batch_create", "qr_batch_picard_step", "qr_batch_info", "qr_batch_set_grouping", "qr_batch_groups",
-    "qr_batch_last_error", "qr_batch_destroy", "qr_fma_peak",
+    "qr_batch_last_error", "qr_batch_destroy", "qr_fma_peak", "qr_tc_selftest",
 ]
 
 
@@ -174,6 +174,8 @@ def load(path: str | None = None):
     L.qr_project_static.argtypes = [vp, vp, C.c_int, C.c_int, vp]
     L.qr_fma_peak.restype = C.c_int
     L.qr_fma_peak.argtypes = [C.c_int, C.c_double, vp, dp, dp, C.POINTER(C.c_int)]
+    L.qr_tc_selftest.restype = C.c_int
+    L.qr_tc_selftest.argtypes = [C.POINTER(C.c_uint16), C.POINTER(C.c_uint16), C.POINTER(C.c_float)]
     _lib = L
     return L
 
@@ -192,3 +194,18 @@ def fma_peak(kind: int, ms: float, stream: int | None = None) -> dict:
     tf, el, sms = C.c_double(), C.c_double(), C.c_int()
     check(L.qr_fma_peak(kind, ms, C.c_void_p(stream or 0), C.byref(tf), C.byref(el), C.byref(sms)))
     return {"tflops": tf.value, "ms": el.value, "sm_count": sms.value}
+
+
+def tc_selftest(A_bits, B_bits):
+    """qr_tc_selftest: D = A B^T (128x64 and 32x64 BF16 bit patterns) on the tensor cores."""
+    import numpy as np
+
+    L = load()
+    A = np.ascontiguousarray(A_bits, dtype=np.uint16)
+    B = np.ascontiguousarray(B_bits, dtype=np.uint16)
+    if A.shape != (128, 64) or B.shape != (32, 64):
+        raise ValueError("A must be 128x64 and B 32x64")
+    D = np.zeros((128, 32), dtype=np.float32)
+    check(L.qr_tc_selftest(A.ctypes.data_as(C.POINTER(C.c_uint16)), B.ctypes.data_as(C.POINTER(C.c_uint16)),
+                           D.ctypes.data_as(C.POINTER(C.c_float))))
+    return D

@@ -21,7 +21,7 @@ OBJ = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libqrmc.so")
 SOURCES = ["qr_kernels.cu", "qr_fast.cu", "qr_fast_more.cu", "qr_proj_tree.cu", "qr_proj_more.cu", "qr_api.cu",
            "qr_static.cu", "qr_mlp.cu", "qr_batch.cu", "qr_group.cu", "qr_fast_paper.cu",
-           "qr_cosine.cu", "qr_peak.cu"]
+           "qr_cosine.cu", "qr_peak.cu", "qr_tc_selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

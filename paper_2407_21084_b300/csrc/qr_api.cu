@@ -179,6 +179,16 @@ bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vect
         out.push_back(b);
         emitted += 2;
     };
+    // slots of a last-dimension node in state S and its chain of extensions
+    auto chain_len = [&](int S) {
+        int len = 1;
+        while (ext_ok(S)) {
+            ++len;
+            if (leaf(d - 1, ext_S(S))) break;
+            S = ext_S(S);
+        }
+        return len;
+    };
     std::function<void(int, int, std::vector<int>)> node = [&](int L, int S, std::vector<int> k) {
         single(k);
         if (ext_ok(S)) {
@@ -194,6 +204,15 @@ bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vect
                 km[l2] -= 1;
                 if (leaf(l2, new_S(S))) {
                     pair(kp, km);
+                } else if (l2 == d - 1) {
+                    // the mirrored chains k +- m e_{d-1} as pairs, m = 1..len
+                    const int len = chain_len(new_S(S));
+                    for (int m = 1; m <= len; ++m) {
+                        std::vector<int> cp = k, cm = k;
+                        cp[l2] += m;
+                        cm[l2] -= m;
+                        pair(cp, cm);
+                    }
                 } else {
                     node(l2, new_S(S), kp);
                     node(l2, new_S(S), km);
@@ -708,6 +727,7 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     default:
         return bail(QR_EINVAL, "unknown driver");
     }
+    for (int j = 0; j < N; ++j) P.fexp32[j] = (float)P.fexp[j];
     P.g_kind = g->kind;
     if (g->kind == QR_GT_COS) {
         if (!g->params || g->n_params < d) return bail(QR_EINVAL, "cos terminal needs {s_1..s_d}");

@@ -61,6 +61,7 @@ struct QrParams {
     int g_kind;  // QR_GT_*
     double g_s[kDMax], g_kap, g_lam;
     double fexp[kNMax];  // time factor of f at t_j
+    float fexp32[kNMax]; // the same, rounded to FP32 (FP32 path kernels)
     uint32_t key0, key1;
     int instance;
     double clamp_L;  // <= 0: off

@@ -1,0 +1,106 @@
+// qr_tc.cuh -- Blackwell (sm_100-family) 5th-generation tensor-core
+// primitives used by the shared-point group kernel: tensor-memory (TMEM)
+// allocation, tcgen05.mma with both operands in shared memory, completion
+// through tcgen05.commit on an mbarrier, and tcgen05.ld of the accumulator.
+//
+// Operand layout (both A = M x K and B = N x K, "K-major"): BF16 tiles of
+// 64 K-elements (128 bytes) per row, rows consecutive, in the 128-byte
+// swizzled layout: the 16-byte chunk c of row r is stored at chunk c ^ (r & 7)
+// of that row, and every tile starts on a 1024-byte boundary (8 rows form one
+// swizzle atom). One MMA consumes K = 16 (32 bytes); the next K-slice of the
+// same tile is addressed by moving the descriptor's start address by 32
+// bytes, the swizzle being a function of the absolute shared address.
+#pragma once
+
+#include <cstdint>
+
+#include "qr_device.cuh"
+
+namespace qr {
+
+// element (r, k) of a swizzled 64-wide BF16 tile: byte offset from the tile base
+__host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t k)
+{
+    return r * 128u + ((((k >> 3) ^ (r & 7u)) & 7u) << 4) + ((k & 7u) << 1);
+}
+
+// shared-memory matrix descriptor: start address, leading/stride byte
+// offsets (>> 4), descriptor version 1, 128-byte swizzle; the stride byte
+// offset is the distance between consecutive 8-row atoms (1024 bytes)
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);    // bits 0-13: start address
+    d |= (uint64_t)(16u >> 4) << 16;             // bits 16-29: leading byte offset (unused when swizzled)
+    d |= (uint64_t)(1024u >> 4) << 32;           // bits 32-45: stride byte offset
+    d |= (uint64_t)1 << 46;                      // bits 46-47: version
+    d |= (uint64_t)2 << 61;                      // bits 61-63: 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N x M tile
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
+{
+    return (1u << 4)                       // D format: F32
+           | (1u << 7)                     // A format: BF16
+           | (1u << 10)                    // B format: BF16
+           | ((uint32_t)(N >> 3) << 17)    // N / 8
+           | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D (TMEM) = A B^T (+ D when accum != 0), issued by one thread
+__device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+// arrive (once) on the mbarrier when every MMA this thread issued so far is done
+__device__ __forceinline__ void tc_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// this warp's 32 TMEM lanes x 32 consecutive columns (32-bit each): thread t
+// receives lane (lane base + t), columns col .. col + 31
+__device__ __forceinline__ void tmem_ld_32x32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
+}
+
+}  // namespace qr

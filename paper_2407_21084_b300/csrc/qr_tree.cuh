@@ -18,6 +18,9 @@
 #ifndef QR_FAST_FCOS
 #define QR_FAST_FCOS 1
 #endif
+#ifndef QR_FAST_UNI
+#define QR_FAST_UNI 1
+#endif
 
 namespace qr {
 
@@ -44,6 +47,26 @@ struct TreeShape {
         for (int l = 0; l < D; ++l) n += leaf(l, root_S()) ? 1 : size(l, root_S());
         return n;
     }
+    // slots of a node (D-1, S) of the last dimension: itself and its chain of
+    // extensions (a node of the last dimension has no new-dimension children)
+    static constexpr int chain_len(int S)
+    {
+        return 1 + (ext_ok(S) ? (leaf(D - 1, ext_S(S)) ? 1 : chain_len(ext_S(S))) : 0);
+    }
+    // powers z_{D-1}^m, m = 1..npow, used by the last-dimension pair chains
+    static constexpr int npow()
+    {
+        const int np = KIND == QR_G_L1 ? NN - 1 : NN;
+        return np < 1 ? 1 : np;
+    }
+};
+
+// the phases of one path point as the tree evaluation sees them: z[p][l] =
+// e^{2 pi i F(x_l)} and the powers zl[p][m] = z[p][D-1]^{m+1}
+template <typename R, int P, int D, int NPW>
+struct TreePh {
+    V2<R> z[P][D];
+    V2<R> zl[P][NPW];
 };
 
 template <typename R>
@@ -93,6 +116,19 @@ __device__ __forceinline__ float u01_f32(uint32_t a, uint32_t b)
     return fmaf((float)(b >> 12), 0x1p-52f, fmaf((float)a, 0x1p-32f, 0x1p-53f));
 }
 
+// The same uniform without integer-to-float conversion instructions (which
+// B300 issues to its narrow FP64 pipe): each piece of n below 2^23 becomes
+// an exact float by placing it in the mantissa of 2^23 and subtracting 2^23,
+// u = (a >> 16) 2^-16 + (a & 0xffff) 2^-32 + (b >> 12) 2^-52 + 2^-53, summed
+// by FMA from the smallest piece up (two roundings in all).
+__device__ __forceinline__ float u01_bits(uint32_t a, uint32_t b)
+{
+    const float fh = __uint_as_float(0x4B000000u | (a >> 16)) - 8388608.0f;
+    const float fl = __uint_as_float(0x4B000000u | (a & 0xFFFFu)) - 8388608.0f;
+    const float fb = __uint_as_float(0x4B000000u | (b >> 12)) - 8388608.0f;
+    return fmaf(fh, 0x1p-16f, fmaf(fl, 0x1p-32f, fmaf(fb, 0x1p-52f, 0x1p-53f)));
+}
+
 template <typename R, int D>
 __device__ __forceinline__ void normals_fast(const QrParams& P, int i, uint32_t m, int j, R (&z)[D])
 {
@@ -109,7 +145,14 @@ __device__ __forceinline__ void normals_fast(const QrParams& P, int i, uint32_t 
             // above 1/2, with v = 1 - u_a from the complemented bits,
             // ln(1 - v) = 2 atanh(s), s = -v / (2 - v), |s| < 1/3, by the odd
             // Taylor series of atanh to s^15 (truncation below 2e-9 relative)
+#if QR_FAST_UNI
+            // t = min(u_a, 1 - u_a) from the integer (complemented words when
+            // u_a >= 1/2, exact); ln u_a = ln t or ln(1 - t)
+            const bool upper = (r.x & 0x80000000u) != 0;
+            const float v = u01_bits(upper ? ~r.x : r.x, upper ? ~r.y : r.y);
+#else
             const float v = u01_f32(~r.x, ~r.y);
+#endif
             const float s = __fdividef(-v, 2.0f - v), s2 = s * s;
             float t = 1.0f / 15.0f;
             t = fmaf(t, s2, 1.0f / 13.0f);
@@ -119,16 +162,24 @@ __device__ __forceinline__ void normals_fast(const QrParams& P, int i, uint32_t 
             t = fmaf(t, s2, 1.0f / 5.0f);
             t = fmaf(t, s2, 1.0f / 3.0f);
             t = fmaf(t, s2, 1.0f);
+#if QR_FAST_UNI
+            const float la = upper ? 2.0f * s * t : __logf(v);
+            const float rr = -2.0f * la;  // >= 2^-52 > 0
+            const float rho = rr * rsqrtf(rr);
+            const float ub = u01_bits(r.z, r.w);
+#else
             const float la = (r.x & 0x80000000u) ? 2.0f * s * t : __logf(u01_f32(r.x, r.y));
             const float rho = sqrtf(-2.0f * la);
+            const float ub = u01_f32(r.z, r.w);
+#endif
             float sn, cs;
 #if QR_FAST_BM
             // (cos, sin)(2 pi u_b) = -(cos, sin)(2 pi (u_b - 1/2)), argument in [-pi, pi]
-            __sincosf(6.28318530717958648f * (u01_f32(r.z, r.w) - 0.5f), &sn, &cs);
+            __sincosf(6.28318530717958648f * (ub - 0.5f), &sn, &cs);
             sn = -sn;
             cs = -cs;
 #else
-            sincospif(2.0f * u01_f32(r.z, r.w), &sn, &cs);
+            sincospif(2.0f * ub, &sn, &cs);
 #endif
             z[2 * c] = rho * cs;
             if (2 * c + 1 < D) z[2 * c + 1] = rho * sn;
@@ -173,7 +224,9 @@ __device__ __forceinline__ R rcos_fast(R a)
 #if QR_FAST_FCOS
     if constexpr (sizeof(R) == 4) {
         if (fabsf(a) < 1048576.0f) {
-            const float k = rintf(a * 0.159154943091895336f);
+            // nearest integer to a/(2 pi) (|.| < 2^18): adding and removing
+            // 1.5 2^23 rounds to an integer in the FMA pipe
+            const float k = fmaf(a, 0.159154943091895336f, 12582912.0f) - 12582912.0f;
             float r = fmaf(-k, 6.28318548202514648f, a);  // float(2 pi)
             r = fmaf(-k, -1.74845553146951715e-7f, r);    // 2 pi - float(2 pi)
             return __cosf(r);
@@ -271,36 +324,56 @@ __device__ __forceinline__ void cmad(V2<R>& t, V2<R> w, V2<R> v)
 // Re V_root. Every tree edge costs one complex FMA (4 FMA); a +-1 leaf pair
 // costs 4 FMA for both leaves; no prefix products are formed.
 
+// T += c+ w + c- conj(w) for a pair of coefficients at the mirrored
+// positions k +- (a step of phase w), pre-combined as the slots (A, C), (B, E):
+// T.x += A w.x + B w.y,  T.y += C w.y + E w.x, i.e.
+// T += (A, C) * (w.x, w.y) + (B, E) * (w.y, w.x) lane-wise; 4 FMA for two
+// coefficients, the sum being real-linear in (Re w, Im w)
+template <typename R>
+__device__ __forceinline__ void pair_acc(V2<R>& T, V2<R> ac, V2<R> be, V2<R> w)
+{
+#if QR_TREE_PAIR2
+    if constexpr (sizeof(R) == 4) {
+        T = __ffma2_rn(ac, w, T);
+        T = __ffma2_rn(be, make_float2(w.y, w.x), T);
+        return;
+    }
+#endif
+    T.x = fma(ac.x, w.x, T.x);
+    T.x = fma(be.x, w.y, T.x);
+    T.y = fma(ac.y, w.y, T.y);
+    T.y = fma(be.y, w.x, T.y);
+}
+
 // children in the new dimensions L2 .. D-1 of a node in state S
 template <typename R, int D, int NN, int KIND, int P, int L2, int S>
 struct NewDims {
     using Sh = TreeShape<D, NN, KIND>;
-    static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, int& off, V2<R> (&T)[P],
-                                               const V2<R> (&z)[P][D])
+    using Ph = TreePh<R, P, D, Sh::npow()>;
+    static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, int& off, V2<R> (&T)[P], const Ph& z)
     {
         if constexpr (L2 < D) {
             constexpr int S2 = Sh::new_S(S);
             if constexpr (Sh::leaf(L2, S2)) {
-                // T += c+ z + c- conj(z), pre-combined as the slots (A, C), (B, E):
-                // T.x += A z.x + B z.y,  T.y += C z.y + E z.x, i.e.
-                // T += (A, C) * (z.x, z.y) + (B, E) * (z.y, z.x) lane-wise
                 const V2<R> ac = c[off], be = c[off + 1];
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
-#if QR_TREE_PAIR2
-                    if constexpr (sizeof(R) == 4) {
-                        const float2 zl = z[p][L2];
-                        T[p] = __ffma2_rn(ac, zl, T[p]);
-                        T[p] = __ffma2_rn(be, make_float2(zl.y, zl.x), T[p]);
-                        continue;
-                    }
-#endif
-                    T[p].x = fma(ac.x, z[p][L2].x, T[p].x);
-                    T[p].x = fma(be.x, z[p][L2].y, T[p].x);
-                    T[p].y = fma(ac.y, z[p][L2].y, T[p].y);
-                    T[p].y = fma(be.y, z[p][L2].x, T[p].y);
-                }
+                for (int p = 0; p < P; ++p) pair_acc<R>(T[p], ac, be, z.z[p][L2]);
                 off += 2;
+            } else if constexpr (L2 == D - 1) {
+                // the + and - chains k +- m e_{D-1}, m = 1..len, of the last
+                // dimension: their contribution in this node's frame,
+                // sum_m (c+_m z^m + c-_m conj(z)^m), is real-linear in the
+                // powers z^m (computed once per point), so each mirrored pair
+                // costs 4 FMA instead of two Horner edges (8 FMA)
+                constexpr int len = Sh::chain_len(S2);
+                static_assert(len <= Sh::npow(), "power table too short");
+#pragma unroll
+                for (int mm = 0; mm < len; ++mm) {
+                    const V2<R> ac = c[off + 2 * mm], be = c[off + 2 * mm + 1];
+#pragma unroll
+                    for (int p = 0; p < P; ++p) pair_acc<R>(T[p], ac, be, z.zl[p][mm]);
+                }
+                off += 2 * len;
             } else {
                 constexpr int sz = Sh::size(L2, S2);
                 const V2<R>* cs = c + off;
@@ -308,7 +381,7 @@ struct NewDims {
                     // small subtrees: both signs unrolled (no loop control)
                     V2<R> w[P], v[P];
 #pragma unroll
-                    for (int p = 0; p < P; ++p) w[p] = z[p][L2];
+                    for (int p = 0; p < P; ++p) w[p] = z.z[p][L2];
                     Node<R, D, NN, KIND, P, L2, S2>::value(cs, w, z, v);
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
@@ -324,7 +397,7 @@ struct NewDims {
                         V2<R> w[P], v[P];
 #pragma unroll
                         for (int p = 0; p < P; ++p) {
-                            w[p] = z[p][L2];
+                            w[p] = z.z[p][L2];
                             if (s) w[p].y = -w[p].y;
                         }
                         Node<R, D, NN, KIND, P, L2, S2>::value(cs + s * sz, w, z, v);
@@ -344,8 +417,9 @@ struct NewDims {
 template <typename R, int D, int NN, int KIND, int P, int L, int S>
 struct Node {
     using Sh = TreeShape<D, NN, KIND>;
-    static __device__ __forceinline__ void value(const V2<R>* __restrict__ c, const V2<R> (&wl)[P],
-                                                 const V2<R> (&z)[P][D], V2<R> (&T)[P])
+    using Ph = TreePh<R, P, D, Sh::npow()>;
+    static __device__ __forceinline__ void value(const V2<R>* __restrict__ c, const V2<R> (&wl)[P], const Ph& z,
+                                                 V2<R> (&T)[P])
     {
         const V2<R> c0 = c[0];
 #pragma unroll
@@ -374,20 +448,20 @@ struct Node {
 template <typename R, int D, int NN, int KIND, int P, int L>
 struct RootKids {
     using Sh = TreeShape<D, NN, KIND>;
-    static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, int& off, V2<R> (&T)[P],
-                                               const V2<R> (&z)[P][D])
+    using Ph = TreePh<R, P, D, Sh::npow()>;
+    static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, int& off, V2<R> (&T)[P], const Ph& z)
     {
         if constexpr (L < D) {
             constexpr int S0 = Sh::root_S();
             if constexpr (Sh::leaf(L, S0)) {
                 const V2<R> ce = c[off];
 #pragma unroll
-                for (int p = 0; p < P; ++p) cfma<R>(T[p], ce, z[p][L]);
+                for (int p = 0; p < P; ++p) cfma<R>(T[p], ce, z.z[p][L]);
                 off += 1;
             } else {
                 V2<R> w[P], v[P];
 #pragma unroll
-                for (int p = 0; p < P; ++p) w[p] = z[p][L];
+                for (int p = 0; p < P; ++p) w[p] = z.z[p][L];
                 Node<R, D, NN, KIND, P, L, S0>::value(c + off, w, z, v);
 #pragma unroll
                 for (int p = 0; p < P; ++p) cmad<R>(T[p], w[p], v[p]);
@@ -401,12 +475,22 @@ struct RootKids {
 template <typename R, int D, int NN, int KIND, int P>
 __device__ __forceinline__ void tree_series(const V2<R>* __restrict__ c, const V2<R> (&z)[P][D], R (&y)[P])
 {
+    using Sh = TreeShape<D, NN, KIND>;
+    TreePh<R, P, D, Sh::npow()> ph;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+#pragma unroll
+        for (int l = 0; l < D; ++l) ph.z[p][l] = z[p][l];
+        ph.zl[p][0] = z[p][D - 1];
+#pragma unroll
+        for (int m = 1; m < Sh::npow(); ++m) ph.zl[p][m] = cmul<R>(ph.zl[p][m - 1], z[p][D - 1]);
+    }
     V2<R> T[P];
     const V2<R> c0 = c[0];
 #pragma unroll
     for (int p = 0; p < P; ++p) T[p] = c0;
     int off = 1;
-    RootKids<R, D, NN, KIND, P, 0>::run(c, off, T, z);
+    RootKids<R, D, NN, KIND, P, 0>::run(c, off, T, ph);
 #pragma unroll
     for (int p = 0; p < P; ++p) y[p] = T[p].x;
 }
@@ -451,7 +535,11 @@ __device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __res
         const int buf = (j - i) & 1, row = j + 1;
         const bool use_series = row < N || trig;
         const int nrow = row + 1;
-        const R fexp_j = (R)Pm.fexp[j];
+        R fexp_j;
+        if constexpr (sizeof(R) == 4)
+            fexp_j = Pm.fexp32[j];
+        else
+            fexp_j = Pm.fexp[j];
         if (nrow < N || (nrow == N && trig)) {
             if (tid == 0) {
                 fence_proxy_async_smem();
