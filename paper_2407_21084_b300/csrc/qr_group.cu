@@ -2,50 +2,55 @@
 // sample points: same d, N, M, sigma, b, index set, density, seed and Philox
 // instance, so every instance sees the same Euler paths and the same basis
 // values; only the coefficients (and the driver/terminal parameters a, s)
-// differ. The series of G instances at a tile of 128 path points is then the
-// dense product
+// differ. The series of G = 32 instances at a tile of 128 path points is then
+// the dense product
 //     Y[128 x G] = Phi[128 x K] A[K x G],   K = 2 |Gamma_+| - 1 (+ padding),
 // Phi = (Re phi_k, Im phi_k) of the half set and A = (2 Re alpha_k,
-// -2 Im alpha_k, alpha_0) of each instance. It runs on the tensor cores as
-// BF16 with split operands: X = X_hi + X_lo (both BF16), Y ~= Phi_hi A_hi +
-// Phi_hi A_lo + Phi_lo A_hi accumulated in FP32 (relative error ~2^-16 per
-// product). Phi is built per step by the compile-time tree of the projection
-// (qr_ptree.cuh), in K-chunks of 32 coefficients; A of the next row is
-// staged by a bulk copy. A CTA handles one tile of paths for G = 32
-// instances; the driver, truncation and response sums stay per instance in
-// FP32 registers.
+// -2 Im alpha_k, alpha_0) of each instance. It runs on the 5th-generation
+// tensor cores (tcgen05.mma, kind::f16) as BF16 with split operands:
+// X = X_hi + X_lo (both BF16), Y ~= Phi_hi A_hi + Phi_hi A_lo + Phi_lo A_hi
+// accumulated in FP32 in tensor memory (relative error ~2^-16 per product).
+// Per step and K-chunk of 64 (32 complex basis values), every thread builds
+// its point's row of Phi with the compile-time tree of the projection
+// (qr_ptree.cuh) straight into the 128-byte swizzled shared-memory layout the
+// tensor core reads (conflict-free 16-byte stores); one thread issues the 12
+// MMAs of the chunk and commits them to an mbarrier, which releases the
+// buffer for the next chunk. The coefficient blocks of the next row, packed
+// in the same swizzled layout by k_pack_group, arrive by one bulk copy per
+// step. After the last chunk each warp reads its 32 rows x 32 instances of
+// the accumulator with tcgen05.ld; the driver, truncation and response sums
+// stay per instance in FP32 registers. Every wait is bounded.
 #include <cuda_bf16.h>
 
 #include "qr_group.h"
 #include "qr_ptree.cuh"
+#include "qr_tc.cuh"
 #include "qr_tree.cuh"
 
 namespace qr {
 
-constexpr int kGBS = 128;   // threads = paths per tile
-constexpr int kGG = 32;     // instances per CTA
-constexpr int kGKC = 64;    // K-chunk (32 complex coefficients)
-constexpr int kGPadA = 8;   // bf16 padding of shared-memory rows (bank spread)
+constexpr int kGBS = 128;  // threads = paths per tile = MMA M
+constexpr int kGG = 32;    // instances per CTA = MMA N (32 TMEM columns)
+constexpr int kGKC = 64;   // K-chunk: 32 complex basis values = one 128-byte row
 
 __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi)
 {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
+template <class TR>
+struct GroupDims {
+    static constexpr int nchunks = (TR::n + 1 + 31) / 32;  // tree nodes + the alpha_0 column
+    static constexpr int K = nchunks * kGKC;
+    static constexpr uint32_t chunk_bytes = kGG * 128;          // 32 instance rows of one K-chunk
+    static constexpr uint32_t block_bytes = nchunks * chunk_bytes;  // hi (or lo) of one row block
+};
 
-// basis values (re, im) of the tree nodes of chunk C for one point, split to bf16 hi/lo into
-// rows hi/lo (kGKC entries); entries past the tree hold the constant 1 (alpha_0) then 0
+// basis values (re, im) of the tree nodes of chunk C for one point, split to
+// BF16 hi/lo pairs; entries past the tree hold the constant 1 (alpha_0) then 0
 template <class TR, int D, int C, int j>
 struct ChunkSlots {
-    static __device__ __forceinline__ void run(const float2 (&z)[D], __nv_bfloat16* hi, __nv_bfloat16* lo)
+    static __device__ __forceinline__ void run(const float2 (&z)[D], uint32_t (&hi)[32], uint32_t (&lo)[32])
     {
         if constexpr (j < 32) {
             constexpr int s = C * 32 + j;
@@ -60,8 +65,8 @@ struct ChunkSlots {
             const __nv_bfloat16 rh = __float2bfloat16_rn(re), ih = __float2bfloat16_rn(im);
             const __nv_bfloat16 rl = __float2bfloat16_rn(re - __bfloat162float(rh));
             const __nv_bfloat16 il = __float2bfloat16_rn(im - __bfloat162float(ih));
-            reinterpret_cast<uint32_t*>(hi)[j] = pack_bf16(rh, ih);  // (re, im) at k = 2j, 2j + 1
-            reinterpret_cast<uint32_t*>(lo)[j] = pack_bf16(rl, il);
+            hi[j] = pack_bf16(rh, ih);  // (re, im) at k = 2j, 2j + 1
+            lo[j] = pack_bf16(rl, il);
             ChunkSlots<TR, D, C, j + 1>::run(z, hi, lo);
         }
     }
@@ -69,87 +74,82 @@ struct ChunkSlots {
 
 template <class TR, int D>
 struct GroupSmem {
-    static constexpr int nchunks = (TR::n + 1 + 31) / 32;  // tree nodes + alpha_0 column
-    static constexpr int K = nchunks * kGKC;
-    __nv_bfloat16 A_hi[kGG][K + kGPadA];  // coefficients, instance-major (B operand, col layout)
-    __nv_bfloat16 A_lo[kGG][K + kGPadA];
-    __nv_bfloat16 P_hi[kGBS][kGKC + kGPadA];  // basis chunk, point-major (A operand, row layout)
-    __nv_bfloat16 P_lo[kGBS][kGKC + kGPadA];
-    float Y[kGBS][kGG + 1];
+    using GD = GroupDims<TR>;
+    uint8_t B_hi[GD::block_bytes];  // coefficient block (B operand, N x K), swizzled
+    uint8_t B_lo[GD::block_bytes];
+    uint8_t P_hi[kGBS * 128];  // basis chunk (A operand, M x 64), swizzled
+    uint8_t P_lo[kGBS * 128];
     GroupInstParams ip[kGG];
     float fexp[kGG][kGroupNMax];
-    uint64_t bar;
+    uint64_t bar_b;    // coefficient block copy
+    uint64_t bar_mma;  // tensor-core completion, one phase per commit
+    uint32_t tslot;    // TMEM address of the accumulator
 };
 
-// one chunk of the GEMM: this warp's 32 rows x 32 instances, K-chunk of 64
-template <class TR, int D>
-__device__ __forceinline__ void gemm_chunk(GroupSmem<TR, D>& sm, int chunk, int warp, int lane, float (&acc)[2][4][4])
-{
-    const int r0 = warp * 32, g = lane >> 2, q = lane & 3;
-#pragma unroll
-    for (int kk = 0; kk < kGKC; kk += 16) {
-        uint32_t ah[2][4], al[2][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int row = r0 + mt * 16 + g;
-            const uint32_t* ph0 = reinterpret_cast<const uint32_t*>(&sm.P_hi[row][kk + 2 * q]);
-            const uint32_t* ph1 = reinterpret_cast<const uint32_t*>(&sm.P_hi[row + 8][kk + 2 * q]);
-            const uint32_t* pl0 = reinterpret_cast<const uint32_t*>(&sm.P_lo[row][kk + 2 * q]);
-            const uint32_t* pl1 = reinterpret_cast<const uint32_t*>(&sm.P_lo[row + 8][kk + 2 * q]);
-            ah[mt][0] = ph0[0];
-            ah[mt][1] = ph1[0];
-            ah[mt][2] = ph0[4];  // k + 8
-            ah[mt][3] = ph1[4];
-            al[mt][0] = pl0[0];
-            al[mt][1] = pl1[0];
-            al[mt][2] = pl0[4];
-            al[mt][3] = pl1[4];
-        }
-        const int kg = chunk * kGKC + kk;
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const int col = nt * 8 + g;
-            const uint32_t* bh = reinterpret_cast<const uint32_t*>(&sm.A_hi[col][kg + 2 * q]);
-            const uint32_t* bl = reinterpret_cast<const uint32_t*>(&sm.A_lo[col][kg + 2 * q]);
-            const uint32_t bhi[2] = {bh[0], bh[4]};
-            const uint32_t blo[2] = {bl[0], bl[4]};
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                mma_bf16(acc[mt][nt], ah[mt], bhi);
-                mma_bf16(acc[mt][nt], ah[mt], blo);
-                mma_bf16(acc[mt][nt], al[mt], bhi);
-            }
-        }
-    }
-}
-
-// the K-chunks of one step: basis chunk into shared memory, then the GEMM
+// one K-chunk of one step: the basis rows into shared memory, then (one
+// thread) the 12 MMAs of the chunk and their commit. Returns false when a
+// bounded wait ran out (block-uniform).
 template <class TR, int D, int C>
 struct GroupChunks {
-    static __device__ __forceinline__ void run(GroupSmem<TR, D>& sm, const float2 (&z)[D], int tid, int warp,
-                                               int lane, float (&acc)[2][4][4])
+    using SM = GroupSmem<TR, D>;
+    using GD = GroupDims<TR>;
+    static __device__ __forceinline__ bool run(SM& sm, const float2 (&z)[D], int tid, uint32_t tmem, uint32_t idesc,
+                                               uint32_t& ph_b, uint32_t& ph_m)
     {
-        if constexpr (C < GroupSmem<TR, D>::nchunks) {
-            ChunkSlots<TR, D, C, 0>::run(z, &sm.P_hi[tid][0], &sm.P_lo[tid][0]);
-            __syncthreads();
-            gemm_chunk<TR, D>(sm, C, warp, lane, acc);
-            __syncthreads();
-            GroupChunks<TR, D, C + 1>::run(sm, z, tid, warp, lane, acc);
+        if constexpr (C < GD::nchunks) {
+            bool ok = true;
+            if constexpr (C > 0) {
+                // the previous chunk's MMAs read the basis buffer
+                ok = mbar_wait(&sm.bar_mma, ph_m);
+                ph_m ^= 1u;
+            } else {
+                // the coefficient block of this row
+                ok = mbar_wait(&sm.bar_b, ph_b);
+                ph_b ^= 1u;
+            }
+            uint32_t hi[32], lo[32];
+            ChunkSlots<TR, D, C, 0>::run(z, hi, lo);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const uint32_t o = (uint32_t)tid * 128u + ((uint32_t)((c ^ tid) & 7) << 4);
+                *reinterpret_cast<uint4*>(sm.P_hi + o) = make_uint4(hi[4 * c], hi[4 * c + 1], hi[4 * c + 2], hi[4 * c + 3]);
+                *reinterpret_cast<uint4*>(sm.P_lo + o) = make_uint4(lo[4 * c], lo[4 * c + 1], lo[4 * c + 2], lo[4 * c + 3]);
+            }
+            fence_proxy_async_smem();  // generic stores -> the tensor core's reads
+            tc_fence_before();
+            if (!__syncthreads_and(ok)) return false;
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t pa = smem_u32(sm.P_hi), pl = smem_u32(sm.P_lo);
+                const uint32_t bh = smem_u32(sm.B_hi) + C * GD::chunk_bytes, bl = smem_u32(sm.B_lo) + C * GD::chunk_bytes;
+#pragma unroll
+                for (int kk = 0; kk < kGKC / 16; ++kk) {
+                    const uint32_t ko = 32u * kk;  // K-slice of 16 BF16 within the 128-byte rows
+                    tc_mma_bf16(tmem, sw128_desc(pa + ko), sw128_desc(bh + ko), idesc, (C > 0 || kk > 0) ? 1u : 0u);
+                    tc_mma_bf16(tmem, sw128_desc(pa + ko), sw128_desc(bl + ko), idesc, 1u);
+                    tc_mma_bf16(tmem, sw128_desc(pl + ko), sw128_desc(bh + ko), idesc, 1u);
+                }
+                tc_commit(&sm.bar_mma);
+            }
+            return GroupChunks<TR, D, C + 1>::run(sm, z, tid, tmem, idesc, ph_b, ph_m);
         }
+        return true;
     }
 };
 
 template <int D, int NN, int KIND>
 __global__ void __launch_bounds__(kGBS) k_paths_group(const __grid_constant__ QrParams P, const GroupInst* __restrict__ inst,
-                                                     int n_inst, const __nv_bfloat16* __restrict__ Apack,
-                                                     long long a_row_elems, int tiles_per_i,
+                                                     int n_inst, const uint8_t* __restrict__ Bpack, int tiles_per_i,
                                                      unsigned* __restrict__ status)
 {
     using TR = FullTree<D, NN, KIND>;
+    using GD = GroupDims<TR>;
     using SM = GroupSmem<TR, D>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SM& sm = *reinterpret_cast<SM*>(smem_raw);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // swizzled tiles start on 1024-byte shared addresses (the launch adds the slack)
+    const uint32_t raw = smem_u32(smem_raw);
+    SM& sm = *reinterpret_cast<SM*>(smem_raw + (((raw + 1023u) & ~1023u) - raw));
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int ntiles_g = (n_inst + kGG - 1) / kGG;
     const int gblk = blockIdx.x % ntiles_g;  // which 32 instances
     const int rest = blockIdx.x / ntiles_g;
@@ -164,10 +164,19 @@ __global__ void __launch_bounds__(kGBS) k_paths_group(const __grid_constant__ Qr
         sm.fexp[g][j] = inst[min(g0 + g, n_inst - 1)].fexp[j];
     }
     if (tid == 0) {
-        mbar_init(&sm.bar, 1);
+        mbar_init(&sm.bar_b, 1);
+        mbar_init(&sm.bar_mma, 1);
         fence_mbar_init();
     }
+    if (warp == 0) {
+        tmem_alloc(&sm.tslot, 32);
+        tmem_relinquish();
+    }
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tslot;
+    constexpr uint32_t idesc = idesc_bf16_f32(kGBS, kGG);
 
     const StepConsts<float, D> KC(P);
     float x[D];
@@ -178,112 +187,109 @@ __global__ void __launch_bounds__(kGBS) k_paths_group(const __grid_constant__ Qr
     float S[kGG];
 #pragma unroll
     for (int g = 0; g < kGG; ++g) S[g] = 0.f;
-    uint32_t phase = 0;
+    uint32_t ph_b = 0, ph_m = 0;
     const float dt = KC.dt;
-    const uint32_t abytes = (uint32_t)(SM::K + kGPadA) * 2u * kGG;  // one of A_hi / A_lo
+    bool failed = false;
 
     for (int j = i; j < N; ++j) {
         const int row = j + 1;
         float z[D], x1[D];
         normals_fast<float, D>(P, i, (uint32_t)m, j, z);
         euler_fast<float, D>(KC, x, z, x1);
+        float y[kGG];
         if (row < N) {
             if (tid == 0) {
                 fence_proxy_async_smem();
-                const __nv_bfloat16* src = Apack + ((size_t)row * ntiles_g + gblk) * 2 * (size_t)a_row_elems;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&sm.bar)),
-                             "r"(2 * abytes)
+                const uint8_t* src = Bpack + ((size_t)row * ntiles_g + gblk) * 2 * (size_t)GD::block_bytes;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&sm.bar_b)),
+                             "r"(2u * GD::block_bytes)
                              : "memory");
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(&sm.A_hi[0][0])),
-                    "l"(src), "r"(abytes), "r"(smem_u32(&sm.bar))
+                        smem_u32(sm.B_hi)),
+                    "l"(src), "r"(GD::block_bytes), "r"(smem_u32(&sm.bar_b))
                     : "memory");
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(&sm.A_lo[0][0])),
-                    "l"(src + a_row_elems), "r"(abytes), "r"(smem_u32(&sm.bar))
+                        smem_u32(sm.B_lo)),
+                    "l"(src + GD::block_bytes), "r"(GD::block_bytes), "r"(smem_u32(&sm.bar_b))
                     : "memory");
             }
             float2 ph[D];
 #pragma unroll
-            for (int l = 0; l < D; ++l) ph[l] = nu_phase<float>(P, x1[l]);
-            const bool ok = mbar_wait(&sm.bar, phase);
-            phase ^= 1u;
-            if (!__syncthreads_and(ok)) {
-                if (tid == 0) atomicOr(status, ST_TIMEOUT);
-                return;
+            for (int l = 0; l < D; ++l) ph[l] = nu_phase_fast<float>(P, x1[l]);
+            bool ok = GroupChunks<TR, D, 0>::run(sm, ph, tid, tmem, idesc, ph_b, ph_m);
+            if (ok) {
+                ok = __syncthreads_and(mbar_wait(&sm.bar_mma, ph_m));  // the last chunk's MMAs
+                ph_m ^= 1u;
             }
-            float acc[2][4][4];
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-            GroupChunks<TR, D, 0>::run(sm, ph, tid, warp, lane, acc);
-            // accumulators -> Y[point][instance]
-            const int g = lane >> 2, q = lane & 3;
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) {
-                    const int r = warp * 32 + mt * 16 + g, c = nt * 8 + 2 * q;
-                    sm.Y[r][c] = acc[mt][nt][0];
-                    sm.Y[r][c + 1] = acc[mt][nt][1];
-                    sm.Y[r + 8][c] = acc[mt][nt][2];
-                    sm.Y[r + 8][c + 1] = acc[mt][nt][3];
-                }
-            __syncthreads();
+            if (!ok) {
+                if (tid == 0) atomicOr(status, ST_TIMEOUT);
+                failed = true;
+                break;
+            }
+            tc_fence_after();
+            tmem_ld_32x32(tmem + ((uint32_t)(warp * 32) << 16), y);
         }
         // per instance: truncation T_L, driver f(t_j, X_j, y) and the response sum
 #pragma unroll
         for (int g = 0; g < kGG; ++g) {
             const GroupInstParams& ip = sm.ip[g];
-            float y;
+            float yv;
             if (row < N) {
-                y = sm.Y[tid][g];
-                if (ip.clamp_L > 0.f) y = fminf(fmaxf(y, -ip.clamp_L), ip.clamp_L);
+                yv = y[g];
+                if (ip.clamp_L > 0.f) yv = fminf(fmaxf(yv, -ip.clamp_L), ip.clamp_L);
             } else {
                 float sg = 0.f;
 #pragma unroll
                 for (int l = 0; l < D; ++l) sg += ip.gs[l] * x1[l];
-                y = rcos<float>(sg);  // g(X_N) = cos(s.X_N)
+                yv = rcos_fast<float>(sg);  // g(X_N) = cos(s.X_N)
             }
             float sf = 0.f;
 #pragma unroll
             for (int l = 0; l < D; ++l) sf += ip.fs[l] * x[l];
-            const float u = sm.fexp[g][j] * rcos<float>(sf);
-            S[g] += (-y * y * y + (ip.f_c * u + u * u * u)) * dt;
-            if (row == N) S[g] += y;
+            const float u = sm.fexp[g][j] * rcos_fast<float>(sf);
+            S[g] += (-yv * yv * yv + (ip.f_c * u + u * u * u)) * dt;
+            if (row == N) S[g] += yv;
         }
 #pragma unroll
         for (int l = 0; l < D; ++l) x[l] = x1[l];
+        tc_fence_before();
         __syncthreads();
     }
-    if (m < P.M) {
+    if (!failed && m < P.M) {
 #pragma unroll
         for (int g = 0; g < kGG; ++g)
             if (g < ng) static_cast<float*>(inst[g0 + g].S)[(size_t)i * (size_t)P.M + (size_t)m] = S[g];
     }
+    // a timed-out wait may leave a copy or MMAs in flight: give them a bounded
+    // chance to land before the tensor memory is released
+    if (failed) {
+        (void)mbar_wait(&sm.bar_b, ph_b);
+        (void)mbar_wait(&sm.bar_mma, ph_m);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 32);
 }
 
-// coefficient blocks of row r, instance block gb: [A_hi (32 x (K+pad))][A_lo (same)]
+// coefficient blocks of row r, instance block gb: [hi][lo], each nchunks K-chunks
+// of 32 instance rows x 64 BF16 in the 128-byte swizzled layout
 template <int D, int NN, int KIND>
 __global__ void k_pack_group(const GroupInst* __restrict__ inst, int n_inst, int nG, int zero_idx,
-                             const int* __restrict__ perm, __nv_bfloat16* __restrict__ Apack, int rows)
+                             const int* __restrict__ perm, uint8_t* __restrict__ Bpack, int rows)
 {
     using TR = FullTree<D, NN, KIND>;
-    using SM = GroupSmem<TR, D>;
-    constexpr int KP = SM::K + kGPadA;
+    using GD = GroupDims<TR>;
+    constexpr int K = GD::K;
     const int ntg = (n_inst + kGG - 1) / kGG;
-    const long long total = (long long)rows * ntg * kGG * KP;
+    const long long total = (long long)rows * ntg * kGG * K;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total) return;
-    const int k = (int)(t % KP);
-    const int g = (int)((t / KP) % kGG);
-    const int gb = (int)((t / ((long long)KP * kGG)) % ntg);
-    const int r = (int)(t / ((long long)KP * kGG * ntg));
+    const int k = (int)(t % K);
+    const int g = (int)((t / K) % kGG);
+    const int gb = (int)((t / ((long long)K * kGG)) % ntg);
+    const int r = (int)(t / ((long long)K * kGG * ntg));
     const int q = gb * kGG + g;
     double v = 0.0;
     if (q < n_inst && k < 2 * TR::n + 1) {
@@ -298,9 +304,10 @@ __global__ void k_pack_group(const GroupInst* __restrict__ inst, int n_inst, int
     const float vf = (float)v;
     const __nv_bfloat16 hi = __float2bfloat16_rn(vf);
     const __nv_bfloat16 lo = __float2bfloat16_rn(vf - __bfloat162float(hi));
-    __nv_bfloat16* base = Apack + ((size_t)r * ntg + gb) * 2 * (size_t)kGG * KP;
-    base[(size_t)g * KP + k] = hi;
-    base[(size_t)kGG * KP + (size_t)g * KP + k] = lo;
+    uint8_t* base = Bpack + ((size_t)r * ntg + gb) * 2 * (size_t)GD::block_bytes;
+    const uint32_t o = (uint32_t)(k / kGKC) * GD::chunk_bytes + sw128_offset((uint32_t)g, (uint32_t)(k % kGKC));
+    *reinterpret_cast<__nv_bfloat16*>(base + o) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(base + GD::block_bytes + o) = lo;
 }
 
 #define QR_GROUP_SETS(X) \
@@ -319,7 +326,7 @@ bool group_supported(int kind, int d, int n)
 long long group_block_elems(int kind, int d, int n)
 {
 #define QR_X(KD, DD, NNN) \
-    if (kind == KD && d == DD && n == NNN) return (long long)kGG * (GroupSmem<FullTree<DD, NNN, KD>, DD>::K + kGPadA);
+    if (kind == KD && d == DD && n == NNN) return (long long)GroupDims<FullTree<DD, NNN, KD>>::block_bytes / 2;
     QR_GROUP_SETS(QR_X)
 #undef QR_X
     return 0;
@@ -333,7 +340,7 @@ cudaError_t launch_pack_group(int kind, int d, int n, const GroupInst* inst, int
     if (kind == KD && d == DD && n == NNN) {                                                                \
         const long long total = (long long)rows * ntg * group_block_elems(KD, DD, NNN);                    \
         k_pack_group<DD, NNN, KD><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(                         \
-            inst, n_inst, nG, zero_idx, perm, static_cast<__nv_bfloat16*>(Apack), rows);                   \
+            inst, n_inst, nG, zero_idx, perm, static_cast<uint8_t*>(Apack), rows);                         \
         return cudaGetLastError();                                                                         \
     }
     QR_GROUP_SETS(QR_X)
@@ -349,14 +356,13 @@ cudaError_t launch_paths_group(int kind, int d, int n, const QrParams& P, const 
     const int tiles = (int)((P.M + kGBS - 1) / kGBS);
 #define QR_X(KD, DD, NNN)                                                                                     \
     if (kind == KD && d == DD && n == NNN) {                                                                  \
-        using SMT = GroupSmem<FullTree<DD, NNN, KD>, DD>;                                                     \
+        constexpr size_t smb = sizeof(GroupSmem<FullTree<DD, NNN, KD>, DD>) + 1024; /* + alignment slack */ \
         auto kern = k_paths_group<DD, NNN, KD>;                                                               \
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SMT)); \
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);    \
         if (e != cudaSuccess) return e;                                                                      \
         const long long blocks = (long long)tiles * P.N * ntg;                                               \
-        kern<<<(unsigned)blocks, kGBS, sizeof(SMT), st>>>(P, inst, n_inst,                                   \
-                                                         static_cast<const __nv_bfloat16*>(Apack),           \
-                                                         group_block_elems(KD, DD, NNN), tiles, status);      \
+        kern<<<(unsigned)blocks, kGBS, smb, st>>>(P, inst, n_inst, static_cast<const uint8_t*>(Apack), tiles,  \
+                                                  status);                                                  \
         return cudaGetLastError();                                                                           \
     }
     QR_GROUP_SETS(QR_X)
