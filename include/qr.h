@@ -326,6 +326,40 @@ qr_status qr_sample(int d, const qr_nu* nu, unsigned long long seed, int instanc
 qr_status qr_sample_normals_tree(int d, unsigned long long seed, int instance, int i, long long m0, long long n,
                                  int j, double* z_out);
 
+/* ---- one problem over several GPUs (Sec. 4's multi-GPU scheme) -------------
+ * The paper splits the Monte-Carlo sum of eq. (Aqi:bar:M) over GPUs by paths
+ * and reduces the per-GPU partial sums in a second level (Sec. 4). Here the
+ * M paths of every row are cut into the projection's chunks, the chunks into
+ * 8 fixed groups (group g = chunks [floor(g C/8), floor((g+1) C/8)), C chunks),
+ * and the cross-chunk sum is always taken as: chunks in order within each
+ * group, then the 8 group sums in order. A rank of a world of W ranks (W in
+ * {1, 2, 4, 8}) owns groups [rank 8/W, (rank+1) 8/W): it simulates and projects
+ * only the paths of those chunks, and the W ranks exchange their group sums
+ * (kShardGroups x N x |Gamma_+| complex doubles, e.g. by an all-gather) once per
+ * iteration. Every rank then holds the coefficients a single GPU computes,
+ * bit for bit, whatever W.
+ *
+ * qr_shard_plan: the chunk and group ranges of `rank` (host arithmetic only;
+ *   QR_EINVAL unless W divides 8, 0 <= rank < W and n_chunks >= 1).
+ * qr_shard: restricts a context (Fourier basis) to its rank's chunks; W = 1
+ *   undoes it. A context with W > 1 iterates by qr_picard_begin (paths,
+ *   projection and the group sums of its own groups, asynchronous on the
+ *   context's stream), the exchange of the group sums by the caller, and
+ *   qr_picard_finish (the reduction from all 8 group sums, repack; blocks;
+ *   residual_out as qr_picard_step). qr_picard_step, qr_backward_sweep,
+ *   qr_project_static and batches refuse sharded contexts (QR_EINVAL).
+ * qr_shard_groups: the device array of group sums (8 groups of
+ *   bytes_per_group bytes, group-major, each N x |Gamma_+| double2 in
+ *   canonical half-set order; nullable until qr_shard with W > 1) and this
+ *   rank's groups [g_lo, g_hi). Before qr_picard_finish the caller fills the
+ *   groups of the other ranks with theirs. Clamp and non-finite counts in
+ *   qr_get_stats are this rank's share. */
+qr_status qr_shard_plan(int n_chunks, int rank, int world, int* c_lo, int* c_hi, int* g_lo, int* g_hi);
+qr_status qr_shard(qr_ctx* ctx, int rank, int world);
+qr_status qr_shard_groups(const qr_ctx* ctx, void** gsum, long long* bytes_per_group, int* g_lo, int* g_hi);
+qr_status qr_picard_begin(qr_ctx* ctx);
+qr_status qr_picard_finish(qr_ctx* ctx, double* residual_out);
+
 /* Test hook (the paper has no counterpart): one 128 x 32 x 64 product
  * D = A B^T on the 5th-generation tensor cores (tcgen05.mma, BF16 operands
  * staged in 128-byte swizzled shared memory, FP32 accumulator in tensor

@@ -32,6 +32,7 @@ EXPORTS = [
     "qr_mlp_gradients", "qr_mlp_train_step", "qr_mlp_last_error", "qr_mlp_destroy",
     "qr_batch_create", "qr_batch_picard_step", "qr_batch_info", "qr_batch_set_grouping", "qr_batch_groups",
     "qr_batch_last_error", "qr_batch_destroy", "qr_fma_peak", "qr_tc_selftest",
+    "qr_shard_plan", "qr_shard", "qr_shard_groups", "qr_picard_begin", "qr_picard_finish",
 ]
 
 
@@ -174,6 +175,17 @@ def load(path: str | None = None):
     L.qr_project_static.argtypes = [vp, vp, C.c_int, C.c_int, vp]
     L.qr_fma_peak.restype = C.c_int
     L.qr_fma_peak.argtypes = [C.c_int, C.c_double, vp, dp, dp, C.POINTER(C.c_int)]
+    ip = C.POINTER(C.c_int)
+    L.qr_shard_plan.restype = C.c_int
+    L.qr_shard_plan.argtypes = [C.c_int, C.c_int, C.c_int, ip, ip, ip, ip]
+    L.qr_shard.restype = C.c_int
+    L.qr_shard.argtypes = [vp, C.c_int, C.c_int]
+    L.qr_shard_groups.restype = C.c_int
+    L.qr_shard_groups.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_longlong), ip, ip]
+    L.qr_picard_begin.restype = C.c_int
+    L.qr_picard_begin.argtypes = [vp]
+    L.qr_picard_finish.restype = C.c_int
+    L.qr_picard_finish.argtypes = [vp, dp]
     L.qr_tc_selftest.restype = C.c_int
     L.qr_tc_selftest.argtypes = [C.POINTER(C.c_uint16), C.POINTER(C.c_uint16), C.POINTER(C.c_float)]
     _lib = L
@@ -209,3 +221,11 @@ def tc_selftest(A_bits, B_bits):
     check(L.qr_tc_selftest(A.ctypes.data_as(C.POINTER(C.c_uint16)), B.ctypes.data_as(C.POINTER(C.c_uint16)),
                            D.ctypes.data_as(C.POINTER(C.c_float))))
     return D
+
+
+def shard_plan(n_chunks: int, rank: int, world: int) -> dict:
+    """qr_shard_plan: chunk and group ranges of a rank (host arithmetic)."""
+    L = load()
+    v = [C.c_int() for _ in range(4)]
+    check(L.qr_shard_plan(n_chunks, rank, world, *[C.byref(x) for x in v]))
+    return {"c_lo": v[0].value, "c_hi": v[1].value, "g_lo": v[2].value, "g_hi": v[3].value}

@@ -47,6 +47,11 @@ struct qr_ctx {
     TreeMap* d_tmap = nullptr;
     int proj_nodes = 0;  // tiled projection kernel compiled for this set
     int* d_perm = nullptr;
+    // one problem sharded over ranks by path chunks (qr_shard): this
+    // context's rank and world size, and the group sums exchanged per iteration
+    int shard_rank = 0, shard_world = 1;
+    bool coefs_changed = true;  // by qr_set_coefs since a batch last packed its group blocks
+    double2* d_gsum = nullptr;  // kShardGroups x N x |Gamma_+|
     // cosine basis on N^d (Lemma ortho:dim1), run as the unfolded Z^d set
     // with half-angle phases; raw projections are symmetrised over the sign
     // orbits (CSR over the canonical order) after every reduction
@@ -295,7 +300,7 @@ void release(qr_ctx* c)
         void* ptrs[] = {c->d_tab,     c->d_first,   c->d_alpha,    c->d_packed,    c->d_S,
                         c->d_partial, c->d_counters, c->d_status,   c->d_tree,      c->d_tmap,
                         c->d_perm,    c->d_alpha_raw, c->d_orb_off, c->d_orb_idx, c->d_cgroups,
-                        c->d_cflags,  c->d_cpos};
+                        c->d_cflags,  c->d_cpos,     c->d_gsum};
         for (void* p : ptrs)
             if (p) cudaFreeAsync(p, c->stream);
         cudaStreamSynchronize(c->stream);
@@ -449,6 +454,7 @@ bool ctx_view(const qr_ctx* c, CtxView* v)
     v->gkind = c->gkind;
     v->gn = c->gn;
     v->perm = c->d_perm;
+    v->sharded = c->shard_world > 1;
     return true;
 }
 void ctx_set_error(qr_ctx* c, const char* msg)
@@ -752,6 +758,8 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     const long long per = (o.M + 256ll * BS - 1) / (256ll * BS);
     P.chunk = (int)(BS * std::max(1ll, per));
     P.n_chunks = (int)((o.M + P.chunk - 1) / P.chunk);
+    P.c_lo = 0;
+    P.c_hi = P.n_chunks;
 
     // device state
     QR_CU(c, cudaGetDevice(&c->device));
@@ -917,6 +925,8 @@ static bool ready(const qr_ctx* c) { return c && c->d_packed; }
 qr_status qr_picard_step(qr_ctx* ctx, int n_iter, double* residual_out)
 {
     if (!ready(ctx)) return QR_EINVAL;
+    if (ctx->shard_world > 1)
+        return fail(ctx, QR_EINVAL, "qr_picard_step: a sharded context iterates by qr_picard_begin/finish");
     if (n_iter < 0) return fail(ctx, QR_EINVAL, "n_iter must be >= 0");
     QR_CU(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
     if (!ctx->profiling && !ctx->graph && !ctx->graph_failed && n_iter > 0) {
@@ -961,6 +971,98 @@ qr_status qr_picard_step(qr_ctx* ctx, int n_iter, double* residual_out)
     return QR_OK;
 }
 
+// ------------------------------------------------------------ sharding
+qr_status qr_shard_plan(int n_chunks, int rank, int world, int* c_lo, int* c_hi, int* g_lo, int* g_hi)
+{
+    if (n_chunks < 1 || world < 1 || world > kShardGroups || kShardGroups % world != 0 || rank < 0 || rank >= world)
+        return QR_EINVAL;
+    const int per = kShardGroups / world;
+    const int gl = rank * per, gh = gl + per;
+    if (g_lo) *g_lo = gl;
+    if (g_hi) *g_hi = gh;
+    if (c_lo) *c_lo = group_chunk(gl, n_chunks);
+    if (c_hi) *c_hi = group_chunk(gh, n_chunks);
+    return QR_OK;
+}
+
+qr_status qr_shard(qr_ctx* ctx, int rank, int world)
+{
+    if (!ready(ctx)) return QR_EINVAL;
+    if (ctx->cosine) return fail(ctx, QR_ENOTIMPL, "qr_shard: the cosine basis is not supported");
+    int cl = 0, ch = 0;
+    if (qr_shard_plan(ctx->P.n_chunks, rank, world, &cl, &ch, nullptr, nullptr) != QR_OK)
+        return fail(ctx, QR_EINVAL, "qr_shard: world must divide 8 and 0 <= rank < world");
+    if (world > 1 && !ctx->d_gsum) {
+        qr_status s = dalloc(ctx, &ctx->d_gsum, sizeof(double2) * kShardGroups * (size_t)ctx->N * ctx->nGp);
+        if (s != QR_OK) return s;
+        QR_CU(ctx, cudaMemsetAsync(ctx->d_gsum, 0, sizeof(double2) * kShardGroups * (size_t)ctx->N * ctx->nGp,
+                                   ctx->stream));
+    }
+    ctx->P.c_lo = cl;
+    ctx->P.c_hi = ch;
+    ctx->shard_rank = rank;
+    ctx->shard_world = world;
+    // the captured iteration has the old chunk range baked in
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+    ctx->graph_failed = false;
+    return QR_OK;
+}
+
+qr_status qr_shard_groups(const qr_ctx* ctx, void** gsum, long long* bytes_per_group, int* g_lo, int* g_hi)
+{
+    if (!ready(ctx)) return QR_EINVAL;
+    if (gsum) *gsum = ctx->d_gsum;
+    if (bytes_per_group) *bytes_per_group = (long long)sizeof(double2) * ctx->N * ctx->nGp;
+    return qr_shard_plan(ctx->P.n_chunks, ctx->shard_rank, ctx->shard_world, nullptr, nullptr, g_lo, g_hi);
+}
+
+qr_status qr_picard_begin(qr_ctx* ctx)
+{
+    if (!ready(ctx)) return QR_EINVAL;
+    if (ctx->cosine) return fail(ctx, QR_ENOTIMPL, "qr_picard_begin: the cosine basis is not supported");
+    if (!ctx->d_gsum) return fail(ctx, QR_EINVAL, "qr_picard_begin: the context is not sharded (qr_shard, world > 1)");
+    QR_CU(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
+    cudaError_t e = ctx->tree_slots ? launch_paths_tree(ctx->prec, ctx->gkind, ctx->gn, ctx->P, ctx->d_tree,
+                                                        ctx->tree_stride, ctx->d_S, 0, ctx->N, ctx->d_counters,
+                                                        ctx->d_status, ctx->stream)
+                                    : launch_paths(ctx->prec, ctx->P, ctx->d_tab, ctx->d_first, ctx->d_packed,
+                                                   ctx->row_stride, ctx->d_S, 0, ctx->N, ctx->d_counters,
+                                                   ctx->d_status, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "path-and-series kernel");
+    e = ctx->proj_nodes ? launch_project_tree(ctx->prec, ctx->gkind, ctx->gn, ctx->P, ctx->d_S, ctx->d_perm,
+                                              ctx->d_partial, 0, ctx->N, ctx->stream)
+                        : launch_project(ctx->prec, ctx->P, ctx->d_tab, ctx->d_first, ctx->d_S, ctx->d_partial, 0,
+                                         ctx->N, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "projection kernel");
+    int gl = 0, gh = 0;
+    qr_shard_plan(ctx->P.n_chunks, ctx->shard_rank, ctx->shard_world, nullptr, nullptr, &gl, &gh);
+    e = launch_group_sums(ctx->P, ctx->d_partial, ctx->d_gsum, gl, gh, 0, ctx->N, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "group sums");
+    return QR_OK;
+}
+
+qr_status qr_picard_finish(qr_ctx* ctx, double* residual_out)
+{
+    if (!ready(ctx)) return QR_EINVAL;
+    if (!ctx->d_gsum) return fail(ctx, QR_EINVAL, "qr_picard_finish: the context is not sharded (qr_shard, world > 1)");
+    QR_CU(ctx, cudaMemsetAsync(ctx->d_counters + CNT_RESID, 0, sizeof(unsigned long long), ctx->stream));
+    cudaError_t e = launch_reduce_groups(ctx->prec, ctx->P, ctx->d_gsum, ctx->d_alpha, ctx->nG, ctx->zero_idx,
+                                         ctx->d_packed, ctx->row_stride, 0, ctx->N, ctx->d_counters, ctx->stream);
+    if (e == cudaSuccess && ctx->tree_slots) e = pack_tree_rows(ctx, 0, ctx->N);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reduction kernel");
+    ctx->stats.iterations++;
+    const long long nonfinite_before = ctx->stats.nonfinite;
+    qr_status s = check_device_status(ctx);
+    if (s != QR_OK) return s;
+    if (residual_out) {
+        unsigned long long bits = ctx->h_counters[CNT_RESID];
+        std::memcpy(residual_out, &bits, sizeof *residual_out);
+    }
+    if (ctx->stats.nonfinite > nonfinite_before) return fail(ctx, QR_ENONFINITE, "non-finite responses");
+    return QR_OK;
+}
+
 qr_status qr_selftest_wait_timeout(qr_ctx* ctx)
 {
     if (!ready(ctx)) return QR_EINVAL;
@@ -975,6 +1077,7 @@ qr_status qr_selftest_wait_timeout(qr_ctx* ctx)
 qr_status qr_backward_sweep(qr_ctx* ctx)
 {
     if (!ready(ctx)) return QR_EINVAL;
+    if (ctx->shard_world > 1) return fail(ctx, QR_EINVAL, "qr_backward_sweep: not for a sharded context");
     QR_CU(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
     for (int i = ctx->N - 1; i >= 0; --i) {
         qr_status s = run_rows(ctx, i, i + 1);
@@ -1082,6 +1185,7 @@ qr_status qr_set_coefs(qr_ctx* ctx, const double* alpha_in)
     }
     QR_CU(ctx, cudaMemcpyAsync(ctx->d_alpha, src, sizeof(double2) * (size_t)ctx->N * ctx->nG,
                                cudaMemcpyHostToDevice, ctx->stream));
+    ctx->coefs_changed = true;
     if (ctx->cos_direct)
         QR_CU(ctx, launch_pack_cos(ctx->prec, ctx->d_alpha, ctx->nG, ctx->d_cpos, ctx->d_packed, ctx->row_stride,
                                    ctx->N, ctx->stream));
@@ -1251,6 +1355,16 @@ struct qr_batch {
     cudaEvent_t ev[2] = {};
     double tune_ms[8] = {};
     std::string err;
+    // one finishing launch (projection, reduction, repacks) for all instances
+    // when every instance has a compiled tiled projection
+    bool fused = false;
+    FinishInst* d_fin = nullptr;
+    FinishGroup* d_fgroups = nullptr;
+    int4* d_fitems = nullptr;
+    long long n_fitems = 0;
+    unsigned* d_row_done = nullptr;
+    unsigned* d_grp_done = nullptr;
+    unsigned long long* d_resid = nullptr;
 };
 
 namespace {
@@ -1312,7 +1426,8 @@ qr_status batch_paths(qr_batch* b)
     if (e == cudaSuccess)
         e = launch_paths_batch(b->d_inst, b->d_items, b->n_items, b->d_next, b->max_rowbytes, b->grid, b->stream);
     for (const BatchGroup& g : b->groups) {
-        if (e == cudaSuccess)
+        // the fused path repacks the group blocks in its finishing kernel
+        if (e == cudaSuccess && !b->fused)
             e = launch_pack_group(g.kind, g.d, g.n, g.d_inst, (int)g.members.size(), g.nG, g.zero_idx, g.d_perm,
                                   g.d_apack, g.P.N, b->stream);
         if (e == cudaSuccess)
@@ -1406,9 +1521,119 @@ qr_status batch_build_groups(qr_batch* b)
     return QR_OK;
 }
 
+void free_finish(qr_batch* b)
+{
+    void* ptrs[] = {b->d_fin, b->d_fgroups, b->d_fitems, b->d_row_done, b->d_grp_done, b->d_resid};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    b->d_fin = nullptr;
+    b->d_fgroups = nullptr;
+    b->d_fitems = nullptr;
+    b->d_row_done = nullptr;
+    b->d_grp_done = nullptr;
+    b->d_resid = nullptr;
+    b->n_fitems = 0;
+    b->fused = false;
+}
+
+// the finishing kernel's instance and group tables, its work items (class
+// by class, then instance, row, chunk) and zeroed arrival counters
+qr_status batch_build_finish(qr_batch* b)
+{
+    free_finish(b);
+    const int n = (int)b->ctx.size();
+    for (const qr_ctx* c : b->ctx)
+        if (!c->proj_nodes || !c->d_perm || c->shard_world != 1) return QR_OK;  // per-instance path
+    std::vector<int> grp_of(n, -1);
+    std::vector<FinishGroup> fg;
+    int grows = 0;
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        const BatchGroup& g = b->groups[gi];
+        const int gcls = finish_group_class(g.kind, g.d, g.n);
+        if (gcls < 0) return QR_OK;
+        for (int q : g.members) grp_of[q] = (int)gi;
+        FinishGroup G{};
+        G.gcls = gcls;
+        G.inst = g.d_inst;
+        G.n_inst = (int)g.members.size();
+        G.nG = g.nG;
+        G.zero_idx = g.zero_idx;
+        G.perm = g.d_perm;
+        G.Bpack = static_cast<uint8_t*>(g.d_apack);
+        G.row_base = grows;
+        grows += g.P.N;
+        fg.push_back(G);
+    }
+    std::vector<FinishInst> fi(n);
+    int rows = 0;
+    for (int q = 0; q < n; ++q) {
+        const qr_ctx* c = b->ctx[q];
+        FinishInst& F = fi[q];
+        std::memset(&F, 0, sizeof F);
+        F.P = c->P;
+        F.cls = batch_class(c->gkind, c->d, c->gn);
+        F.S = static_cast<const float*>(c->d_S);
+        F.partial = c->d_partial;
+        F.alpha = c->d_alpha;
+        F.packed = static_cast<float2*>(c->d_packed);
+        F.row_stride = c->row_stride;
+        F.tree = static_cast<float2*>(c->d_tree);
+        F.tree_stride = c->tree_stride;
+        F.tmap = c->d_tmap;
+        F.tree_slots = c->tree_slots;
+        F.perm = c->d_perm;
+        F.nG = c->nG;
+        F.zero_idx = c->zero_idx;
+        F.row_base = rows;
+        F.group = grp_of[q];
+        rows += c->N;
+    }
+    std::vector<int4> items;
+    for (int cls = 0; cls < 64; ++cls)
+        for (int q = 0; q < n; ++q) {
+            if (fi[q].cls != cls) continue;
+            for (int i = 0; i < b->ctx[q]->N; ++i)
+                for (int ch = 0; ch < fi[q].P.n_chunks; ++ch) items.push_back(make_int4(q, i, ch, 0));
+        }
+    const bool ok =
+        cudaMalloc(&b->d_fin, sizeof(FinishInst) * n) == cudaSuccess &&
+        cudaMalloc(&b->d_fgroups, sizeof(FinishGroup) * std::max<size_t>(1, fg.size())) == cudaSuccess &&
+        cudaMalloc(&b->d_fitems, sizeof(int4) * std::max<size_t>(1, items.size())) == cudaSuccess &&
+        cudaMalloc(&b->d_row_done, sizeof(unsigned) * std::max(1, rows)) == cudaSuccess &&
+        cudaMalloc(&b->d_grp_done, sizeof(unsigned) * std::max(1, grows)) == cudaSuccess &&
+        cudaMalloc(&b->d_resid, sizeof(unsigned long long) * n) == cudaSuccess;
+    if (!ok) {
+        free_finish(b);
+        return bfail(b, QR_ENOMEM, "batch finishing tables");
+    }
+    if (cudaMemcpy(b->d_fin, fi.data(), sizeof(FinishInst) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (!fg.empty() && cudaMemcpy(b->d_fgroups, fg.data(), sizeof(FinishGroup) * fg.size(), cudaMemcpyHostToDevice) !=
+                            cudaSuccess) ||
+        cudaMemcpy(b->d_fitems, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->d_row_done, 0, sizeof(unsigned) * std::max(1, rows)) != cudaSuccess ||
+        cudaMemset(b->d_grp_done, 0, sizeof(unsigned) * std::max(1, grows)) != cudaSuccess) {
+        free_finish(b);
+        return bfail(b, QR_ECUDA, "copy batch finishing tables");
+    }
+    b->n_fitems = (long long)items.size();
+    b->fused = true;
+    return QR_OK;
+}
+
+// projection, reduction and repacks of every instance in one launch
+qr_status batch_rest_fused(qr_batch* b)
+{
+    cudaError_t e = cudaMemsetAsync(b->d_resid, 0, sizeof(unsigned long long) * b->ctx.size(), b->stream);
+    if (e == cudaSuccess)
+        e = launch_finish_batch(b->d_fin, b->d_fitems, b->n_fitems, b->d_fgroups, b->d_row_done, b->d_grp_done,
+                                b->d_resid, b->stream);
+    return e == cudaSuccess ? QR_OK : bfail(b, QR_ECUDA, std::string("batch finishing kernel: ") + cudaGetErrorString(e));
+}
+
 // projection, reduction and repack of every instance (single-instance kernels)
 qr_status batch_rest(qr_batch* b)
 {
+    if (b->fused) return batch_rest_fused(b);
     for (qr_ctx* c : b->ctx) {
         cudaError_t e = cudaMemsetAsync(c->d_counters + CNT_RESID, 0, sizeof(unsigned long long), b->stream);
         if (e == cudaSuccess)
@@ -1445,6 +1670,7 @@ qr_status qr_batch_create(qr_batch** out, qr_ctx* const* ctxs, int n)
         if (!ready(c)) return bfail(b, QR_EINVAL, "batch: instance " + std::to_string(q) + " is not a context");
         if (c->prec != QR_FP32) return bfail(b, QR_EINVAL, "batch: instances must use QR_FP32");
         if (c->cosine) return bfail(b, QR_ENOTIMPL, "batch: the cosine basis is not supported");
+        if (c->shard_world > 1) return bfail(b, QR_EINVAL, "batch: instances must not be sharded");
         const int cls = batch_class(c->gkind, c->d, c->gn);
         if (cls < 0 || !c->tree_slots)
             return bfail(b, QR_ENOTIMPL, "batch: index set of instance " + std::to_string(q) + " has no compiled class");
@@ -1475,6 +1701,7 @@ qr_status qr_batch_create(qr_batch** out, qr_ctx* const* ctxs, int n)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     b->grid = per_sm * sms;
     qr_status gs = batch_build_groups(b);
+    if (gs == QR_OK) gs = batch_build_finish(b);
     if (gs != QR_OK) return gs;
     return batch_set_items(b, 4);
 }
@@ -1485,6 +1712,7 @@ qr_status qr_batch_set_grouping(qr_batch* b, int min_group)
     if (b->tuned) return bfail(b, QR_EINVAL, "batch: grouping is fixed after the first iteration");
     b->group_min = min_group;
     qr_status s = batch_build_groups(b);
+    if (s == QR_OK) s = batch_build_finish(b);
     return s == QR_OK ? batch_set_items(b, b->tiles_per_item) : s;
 }
 
@@ -1504,6 +1732,18 @@ qr_status qr_batch_picard_step(qr_batch* b, int n_iter, double* max_residual)
     for (qr_ctx* c : b->ctx)
         if (cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), b->stream) != cudaSuccess)
             return bfail(b, QR_ECUDA, "reset status");
+    // the fused path repacks group blocks from the finished rows; coefficients
+    // set from the host since then (or never packed) are packed here
+    if (b->fused)
+        for (const BatchGroup& g : b->groups) {
+            bool changed = false;
+            for (int q : g.members) changed = changed || b->ctx[q]->coefs_changed;
+            if (!changed) continue;
+            if (launch_pack_group(g.kind, g.d, g.n, g.d_inst, (int)g.members.size(), g.nG, g.zero_idx, g.d_perm,
+                                  g.d_apack, g.P.N, b->stream) != cudaSuccess)
+                return bfail(b, QR_ECUDA, "group coefficient blocks");
+            for (int q : g.members) b->ctx[q]->coefs_changed = false;
+        }
     if (!b->tuned && n_iter > 0) {
         // autotuner: time the persistent kernel for a few item sizes and
         // grids on the first iteration (it only rewrites the responses)
@@ -1573,9 +1813,22 @@ qr_status qr_batch_picard_step(qr_batch* b, int n_iter, double* max_residual)
             continue;
         }
         if (c->stats.nonfinite > before) worst = QR_ENONFINITE;
-        double r;
-        std::memcpy(&r, &c->h_counters[CNT_RESID], sizeof r);
-        rmax = std::max(rmax, r);
+        if (!b->fused) {
+            double r;
+            std::memcpy(&r, &c->h_counters[CNT_RESID], sizeof r);
+            rmax = std::max(rmax, r);
+        }
+    }
+    if (b->fused && n_iter > 0) {
+        std::vector<unsigned long long> h(b->ctx.size());
+        if (cudaMemcpy(h.data(), b->d_resid, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return bfail(b, QR_ECUDA, "read residuals");
+        for (unsigned long long bits : h) {
+            double r;
+            std::memcpy(&r, &bits, sizeof r);
+            rmax = std::max(rmax, r);
+        }
     }
     if (max_residual) *max_residual = n_iter > 0 ? rmax : 0.0;
     return worst;
@@ -1600,6 +1853,7 @@ void qr_batch_destroy(qr_batch* b)
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_next) cudaFree(b->d_next);
+    free_finish(b);
     free_groups(b);
     for (auto& e : b->ev)
         if (e) cudaEventDestroy(e);

@@ -12,9 +12,16 @@
 // rows are staged in a double buffer sized for the largest row; mbarrier
 // phases carry over from item to item.
 //
-// Projection and reduction reuse the single-instance kernels, one launch per
-// instance, and the whole iteration (counter resets, the persistent kernel,
-// the projections and reductions) is captured in one CUDA graph. The items
+// Projection, reduction and repacks of every instance are ONE more launch
+// (k_finish_batch): a block per (instance, row, chunk of paths), ordered
+// class by class, projects its chunk with the instance's compiled tiled
+// projection; the last chunk of a row to finish (an arrival counter per row)
+// reduces the row -- the same fixed-order two-level chunk sum as a single
+// run, so the coefficients are bit-identical -- and rebuilds the row's tree
+// layout, and the last member of a shared-point group to finish a row
+// repacks the group's tensor-core coefficient blocks of that row. The whole
+// iteration (counter resets, the persistent path kernel, the shared-point
+// kernels, the finishing kernel) is captured in one CUDA graph. The items
 // per claim (tiles per item) and the grid of the persistent kernel are chosen
 // by timing candidates on the first iteration (autotuner).
 #include <algorithm>
@@ -23,6 +30,9 @@
 #include <vector>
 
 #include "qr_batch.h"
+#include "qr_groupdev.cuh"
+#include "qr_ptree.cuh"
+#include "qr_reduce.cuh"
 #include "qr_tree.cuh"
 
 namespace qr {
@@ -123,5 +133,123 @@ int batch_blocks_per_sm(size_t max_rowbytes)
 }
 
 int batch_tile_paths() { return kBatchBS * kBatchP; }
+
+// ---------------------------------------------------------------- finishing
+constexpr int kFinBS = 128, kFinSC = 1024;  // as the single-instance FP32 tiled projection
+
+#define QR_GROUP_CLASSES(X) \
+    X(0, QR_G_LINF, 2, 4)   \
+    X(1, QR_G_L1, 6, 3)
+
+int finish_group_class(int kind, int d, int n)
+{
+#define QR_X(C, K, DD, NNN) \
+    if (kind == K && d == DD && n == NNN) return C;
+    QR_GROUP_CLASSES(QR_X)
+#undef QR_X
+    return -1;
+}
+
+size_t finish_smem()
+{
+    size_t m = 16;
+#define QR_X(C, K, DD, NNN) \
+    m = std::max(m, sizeof(ProjSmem<float, DD, FullTree<DD, NNN, K>, kFinBS, kFinSC>));
+    QR_BATCH_CLASSES(QR_X)
+#undef QR_X
+    return m;
+}
+
+// one (instance, row, chunk) per block; see the file comment
+__global__ void __launch_bounds__(kFinBS) k_finish_batch(const FinishInst* __restrict__ fin,
+                                                         const int4* __restrict__ items,
+                                                         const FinishGroup* __restrict__ groups,
+                                                         unsigned* __restrict__ row_done,
+                                                         unsigned* __restrict__ grp_done,
+                                                         unsigned long long* __restrict__ resid)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_last;
+    const int4 it = items[blockIdx.x];
+    const FinishInst& F = fin[it.x];
+    const QrParams& P = F.P;
+    const int i = it.y, ch = it.z, tid = threadIdx.x;
+    switch (F.cls) {
+#define QR_X(C, K, DD, NNN)                                                                                       \
+    case C:                                                                                                       \
+        project_tree_item<float, DD, NNN, K, kFinBS, kFinSC>(P, F.S + (size_t)i * (size_t)P.M, F.perm,            \
+                                                            F.partial + ((size_t)i * P.n_chunks + ch) * P.nGp, i, \
+                                                            ch, smem);                                            \
+        break;
+        QR_BATCH_CLASSES(QR_X)
+#undef QR_X
+    default:
+        break;
+    }
+    // the last chunk of row i to arrive reduces the row (partials of the
+    // other blocks made visible by their fence before the count)
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned prev = atomicAdd(&row_done[F.row_base + i], 1u);
+        s_last = prev == (unsigned)(P.n_chunks - 1);
+        if (s_last) row_done[F.row_base + i] = 0u;  // ready for the next iteration
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double diff = 0.0;
+    for (int e = tid; e < P.nGp; e += kFinBS) {
+        double sx, sy, dv = 0.0;
+        chunk_sum2(F.partial + (size_t)i * P.n_chunks * P.nGp + e, P.n_chunks, P.nGp, sx, sy);
+        finish_coef<float>(P, sx, sy, e, i, F.nG, F.zero_idx, F.alpha, F.packed, F.row_stride, dv);
+        diff = fmax(diff, dv);
+    }
+    reduce_residual(diff, &resid[it.x]);  // includes a block barrier: the master row is complete
+    const double* a = reinterpret_cast<const double*>(F.alpha + (size_t)i * F.nG);
+    for (int s = tid; s < F.tree_slots; s += kFinBS) F.tree[(size_t)i * F.tree_stride + s] = tree_slot<float>(a, F.tmap[s]);
+    if (F.group < 0) return;
+    // the last member of the group to finish row i repacks the group's row
+    __threadfence();
+    __syncthreads();
+    const FinishGroup& G = groups[F.group];
+    if (tid == 0) {
+        const unsigned prev = atomicAdd(&grp_done[G.row_base + i], 1u);
+        s_last = prev == (unsigned)(G.n_inst - 1);
+        if (s_last) grp_done[G.row_base + i] = 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int ntg = (G.n_inst + kGG - 1) / kGG;
+    switch (G.gcls) {
+#define QR_X(C, KD, DD, NNN)                                                                                   \
+    case C: {                                                                                                 \
+        constexpr int KK = GroupDims<FullTree<DD, NNN, KD>>::K;                                                \
+        const int total = ntg * kGG * KK;                                                                     \
+        for (int t = tid; t < total; t += kFinBS)                                                             \
+            pack_group_elem<DD, NNN, KD>(G.inst, G.n_inst, G.nG, G.zero_idx, G.perm, G.Bpack, ntg, i,          \
+                                        t / (kGG * KK), (t / KK) % kGG, t % KK);                              \
+        break;                                                                                                \
+    }
+        QR_GROUP_CLASSES(QR_X)
+#undef QR_X
+    default:
+        break;
+    }
+}
+
+cudaError_t launch_finish_batch(const FinishInst* fin, const int4* items, long long n_items, const FinishGroup* groups,
+                                unsigned* row_done, unsigned* grp_done, unsigned long long* resid, cudaStream_t st)
+{
+    const size_t sm = finish_smem();
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(k_finish_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    if (n_items <= 0) return cudaSuccess;
+    if (n_items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_finish_batch<<<(unsigned)n_items, kFinBS, sm, st>>>(fin, items, groups, row_done, grp_done, resid);
+    return cudaGetLastError();
+}
 
 }  // namespace qr

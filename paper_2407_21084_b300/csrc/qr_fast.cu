@@ -20,6 +20,7 @@
 // layout", one float2/double2 slot per half-set coefficient) by k_pack_tree
 // and staged in shared memory by bulk copies, double buffered.
 
+#include "qr_reduce.cuh"
 #include "qr_tree.cuh"
 
 namespace qr {
@@ -31,17 +32,7 @@ __global__ void k_pack_tree(const double* __restrict__ alpha, int nG, const Tree
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)rows * slots) return;
     const int r = (int)(idx / slots), s = (int)(idx % slots);
-    const double* a = alpha + (size_t)r * 2 * nG;
-    const TreeMap mp = map[s];
-    double v[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        double t = 0.0;
-        if (mp.c[h][0] != 0) t += mp.c[h][0] * a[mp.i[h][0]];
-        if (mp.c[h][1] != 0) t += mp.c[h][1] * a[mp.i[h][1]];
-        v[h] = t;
-    }
-    out[(size_t)r * row_stride + s] = mk2<R>((R)v[0], (R)v[1]);
+    out[(size_t)r * row_stride + s] = tree_slot<R>(alpha + (size_t)r * 2 * nG, map[s]);
 }
 
 // ------------------------------------------------------------ dispatch

@@ -20,31 +20,15 @@
 // step. After the last chunk each warp reads its 32 rows x 32 instances of
 // the accumulator with tcgen05.ld; the driver, truncation and response sums
 // stay per instance in FP32 registers. Every wait is bounded.
-#include <cuda_bf16.h>
-
-#include "qr_group.h"
-#include "qr_ptree.cuh"
-#include "qr_tc.cuh"
+#include "qr_groupdev.cuh"
 #include "qr_tree.cuh"
 
 namespace qr {
-
-constexpr int kGBS = 128;  // threads = paths per tile = MMA M
-constexpr int kGG = 32;    // instances per CTA = MMA N (32 TMEM columns)
-constexpr int kGKC = 64;   // K-chunk: 32 complex basis values = one 128-byte row
 
 __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi)
 {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
-
-template <class TR>
-struct GroupDims {
-    static constexpr int nchunks = (TR::n + 1 + 31) / 32;  // tree nodes + the alpha_0 column
-    static constexpr int K = nchunks * kGKC;
-    static constexpr uint32_t chunk_bytes = kGG * 128;          // 32 instance rows of one K-chunk
-    static constexpr uint32_t block_bytes = nchunks * chunk_bytes;  // hi (or lo) of one row block
-};
 
 // basis values (re, im) of the tree nodes of chunk C for one point, split to
 // BF16 hi/lo pairs; entries past the tree hold the constant 1 (alpha_0) then 0
@@ -81,6 +65,7 @@ struct GroupSmem {
     uint8_t P_lo[kGBS * 128];
     GroupInstParams ip[kGG];
     float fexp[kGG][kGroupNMax];
+    float S[kGG][kGBS];  // response sums, one column per thread (conflict-free)
     uint64_t bar_b;    // coefficient block copy
     uint64_t bar_mma;  // tensor-core completion, one phase per commit
     uint32_t tslot;    // TMEM address of the accumulator
@@ -184,9 +169,7 @@ __global__ void __launch_bounds__(kGBS) k_paths_group(const __grid_constant__ Qr
         float2 unused[D];
         start_point<float, D>(P, i, m, x, unused, false);
     }
-    float S[kGG];
-#pragma unroll
-    for (int g = 0; g < kGG; ++g) S[g] = 0.f;
+    for (int g = 0; g < kGG; ++g) sm.S[g][tid] = 0.f;
     uint32_t ph_b = 0, ph_m = 0;
     const float dt = KC.dt;
     bool failed = false;
@@ -196,7 +179,6 @@ __global__ void __launch_bounds__(kGBS) k_paths_group(const __grid_constant__ Qr
         float z[D], x1[D];
         normals_fast<float, D>(P, i, (uint32_t)m, j, z);
         euler_fast<float, D>(KC, x, z, x1);
-        float y[kGG];
         if (row < N) {
             if (tid == 0) {
                 fence_proxy_async_smem();
@@ -229,28 +211,36 @@ __global__ void __launch_bounds__(kGBS) k_paths_group(const __grid_constant__ Qr
                 break;
             }
             tc_fence_after();
-            tmem_ld_32x32(tmem + ((uint32_t)(warp * 32) << 16), y);
         }
-        // per instance: truncation T_L, driver f(t_j, X_j, y) and the response sum
+        // per instance: truncation T_L, driver f(t_j, X_j, y) and the response
+        // sum; instances in groups of 8 (a rolled loop keeps the code short),
+        // the series of 8 instances read from 8 accumulator columns at a time
+#pragma unroll 1
+        for (int g8 = 0; g8 < kGG; g8 += 8) {
+            float y8[8];
+            if (row < N) tmem_ld_32x8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)g8, y8);
 #pragma unroll
-        for (int g = 0; g < kGG; ++g) {
-            const GroupInstParams& ip = sm.ip[g];
-            float yv;
-            if (row < N) {
-                yv = y[g];
-                if (ip.clamp_L > 0.f) yv = fminf(fmaxf(yv, -ip.clamp_L), ip.clamp_L);
-            } else {
-                float sg = 0.f;
+            for (int q = 0; q < 8; ++q) {
+                const int g = g8 + q;
+                const GroupInstParams& ip = sm.ip[g];
+                float yv;
+                if (row < N) {
+                    yv = y8[q];
+                    if (ip.clamp_L > 0.f) yv = fminf(fmaxf(yv, -ip.clamp_L), ip.clamp_L);
+                } else {
+                    float sg = 0.f;
 #pragma unroll
-                for (int l = 0; l < D; ++l) sg += ip.gs[l] * x1[l];
-                yv = rcos_fast<float>(sg);  // g(X_N) = cos(s.X_N)
+                    for (int l = 0; l < D; ++l) sg += ip.gs[l] * x1[l];
+                    yv = rcos_fast<float>(sg);  // g(X_N) = cos(s.X_N)
+                }
+                float sf = 0.f;
+#pragma unroll
+                for (int l = 0; l < D; ++l) sf += ip.fs[l] * x[l];
+                const float u = sm.fexp[g][j] * rcos_fast<float>(sf);
+                float Sg = sm.S[g][tid] + (-yv * yv * yv + (ip.f_c * u + u * u * u)) * dt;
+                if (row == N) Sg += yv;
+                sm.S[g][tid] = Sg;
             }
-            float sf = 0.f;
-#pragma unroll
-            for (int l = 0; l < D; ++l) sf += ip.fs[l] * x[l];
-            const float u = sm.fexp[g][j] * rcos_fast<float>(sf);
-            S[g] += (-yv * yv * yv + (ip.f_c * u + u * u * u)) * dt;
-            if (row == N) S[g] += yv;
         }
 #pragma unroll
         for (int l = 0; l < D; ++l) x[l] = x1[l];
@@ -258,9 +248,8 @@ __global__ void __launch_bounds__(kGBS) k_paths_group(const __grid_constant__ Qr
         __syncthreads();
     }
     if (!failed && m < P.M) {
-#pragma unroll
-        for (int g = 0; g < kGG; ++g)
-            if (g < ng) static_cast<float*>(inst[g0 + g].S)[(size_t)i * (size_t)P.M + (size_t)m] = S[g];
+        for (int g = 0; g < ng; ++g)
+            static_cast<float*>(inst[g0 + g].S)[(size_t)i * (size_t)P.M + (size_t)m] = sm.S[g][tid];
     }
     // a timed-out wait may leave a copy or MMAs in flight: give them a bounded
     // chance to land before the tensor memory is released
@@ -279,35 +268,16 @@ template <int D, int NN, int KIND>
 __global__ void k_pack_group(const GroupInst* __restrict__ inst, int n_inst, int nG, int zero_idx,
                              const int* __restrict__ perm, uint8_t* __restrict__ Bpack, int rows)
 {
-    using TR = FullTree<D, NN, KIND>;
-    using GD = GroupDims<TR>;
-    constexpr int K = GD::K;
+    using GD = GroupDims<FullTree<D, NN, KIND>>;
     const int ntg = (n_inst + kGG - 1) / kGG;
-    const long long total = (long long)rows * ntg * kGG * K;
+    const long long total = (long long)rows * ntg * kGG * GD::K;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total) return;
-    const int k = (int)(t % K);
-    const int g = (int)((t / K) % kGG);
-    const int gb = (int)((t / ((long long)K * kGG)) % ntg);
-    const int r = (int)(t / ((long long)K * kGG * ntg));
-    const int q = gb * kGG + g;
-    double v = 0.0;
-    if (q < n_inst && k < 2 * TR::n + 1) {
-        const double2* row = inst[q].alpha + (size_t)r * nG;
-        if (k == 2 * TR::n) {
-            v = row[zero_idx].x;
-        } else {
-            const double2 a = row[zero_idx + perm[k >> 1]];
-            v = (k & 1) ? -2.0 * a.y : 2.0 * a.x;
-        }
-    }
-    const float vf = (float)v;
-    const __nv_bfloat16 hi = __float2bfloat16_rn(vf);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(vf - __bfloat162float(hi));
-    uint8_t* base = Bpack + ((size_t)r * ntg + gb) * 2 * (size_t)GD::block_bytes;
-    const uint32_t o = (uint32_t)(k / kGKC) * GD::chunk_bytes + sw128_offset((uint32_t)g, (uint32_t)(k % kGKC));
-    *reinterpret_cast<__nv_bfloat16*>(base + o) = hi;
-    *reinterpret_cast<__nv_bfloat16*>(base + GD::block_bytes + o) = lo;
+    const int k = (int)(t % GD::K);
+    const int g = (int)((t / GD::K) % kGG);
+    const int gb = (int)((t / ((long long)GD::K * kGG)) % ntg);
+    const int r = (int)(t / ((long long)GD::K * kGG * ntg));
+    pack_group_elem<D, NN, KIND>(inst, n_inst, nG, zero_idx, perm, Bpack, ntg, r, gb, g, k);
 }
 
 #define QR_GROUP_SETS(X) \

@@ -68,10 +68,21 @@ struct QrParams {
     int lattice_n;
     int chunk;     // projection: paths per CTA
     int n_chunks;  // ceil(M / chunk)
+    int c_lo, c_hi;  // chunks this context simulates and projects (a shard of paths; all by default)
     int half_angle;  // cosine basis: phases e^{i pi F(x)} instead of e^{2 pi i F(x)}
     double q_damp;   // damping exponent q of eq. (yqi); 0: none
 };
 
+// The cross-chunk sum of the projection is taken in two fixed levels: the
+// chunks of each of kShardGroups groups in order, then the group sums in
+// order. A shard of a problem over W ranks (W dividing kShardGroups) owns
+// whole groups, so W ranks that exchange their group sums reproduce the
+// one-GPU coefficients bit for bit.
+constexpr int kShardGroups = 8;
+__host__ __device__ inline int group_chunk(int g, int n_chunks)
+{
+    return (int)(((long long)g * n_chunks) / kShardGroups);
+}
 // kernel launchers (qr_kernels.cu); all asynchronous on `st`
 cudaError_t launch_paths(int prec, const QrParams& P, const GEntry* tab, const uint8_t* first,
                          const void* packed, long long row_stride, void* S, int i_lo, int i_hi,
@@ -99,6 +110,24 @@ cudaError_t launch_sample(int prec, const QrParams& P, int i, long long m0, long
 cudaError_t launch_normals_tree(const QrParams& P, int i, long long m0, long long n, int j, double* z,
                                 cudaStream_t st);
 
+// first path of the context's chunk range, and the end of that range
+__host__ __device__ inline long long shard_m_lo(const QrParams& P) { return (long long)P.c_lo * P.chunk; }
+__host__ __device__ inline long long shard_m_hi(const QrParams& P)
+{
+    const long long e = (long long)P.c_hi * P.chunk;
+    return e < P.M ? e : P.M;
+}
+
+// group sums of the chunk partials: gsum[g][row][e] for the groups
+// [g_lo, g_hi) (rows i_lo .. i_hi-1; partial rows relative to i_lo)
+cudaError_t launch_group_sums(const QrParams& P, const double2* partial, double2* gsum, int g_lo, int g_hi, int i_lo,
+                              int i_hi, cudaStream_t st);
+// the reduction from all kShardGroups group sums (as launch_reduce does from
+// the partials): alpha, packed rows, residual
+cudaError_t launch_reduce_groups(int prec, const QrParams& P, const double2* gsum, double2* alpha, int nG, int zero_idx,
+                                 void* packed, long long row_stride, int i_lo, int i_hi,
+                                 unsigned long long* counters, cudaStream_t st);
+
 // read-only view of a context's device problem description (qr_api.cu)
 struct CtxView {
     int prec, N, nG, zero_idx;
@@ -110,6 +139,7 @@ struct CtxView {
     int proj_nodes;  // nonzero: a compiled tiled projection covers the index set
     int gkind, gn;   // its index-set kind and level
     const int* perm; // its slot -> canonical half-set order
+    bool sharded;    // restricted to a chunk range by qr_shard
 };
 }  // namespace qr
 

@@ -24,6 +24,7 @@
 #include <cstdio>
 
 #include "qr_device.cuh"
+#include "qr_reduce.cuh"
 
 namespace qr {
 
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(BS) k_paths(const __grid_constant__ QrParams P
 
     const int tid = threadIdx.x;
     const int i = i_lo + (int)(blockIdx.x / tiles_per_i);
-    const long long m = (long long)(blockIdx.x % tiles_per_i) * BS + tid;
+    const long long m = shard_m_lo(P) + (long long)(blockIdx.x % tiles_per_i) * BS + tid;
     const bool active = m < P.M;
     const bool trig = P.g_kind == QR_GT_TRIGPOLY;
 
@@ -280,8 +281,9 @@ __global__ void __launch_bounds__(BS) k_project(const __grid_constant__ QrParams
     V2<R>* acc = reinterpret_cast<V2<R>*>(smem + off);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int i = i_lo + (int)(blockIdx.x / P.n_chunks);
-    const int ch = (int)(blockIdx.x % P.n_chunks);
+    const int nc = P.c_hi - P.c_lo;  // the context's chunks
+    const int i = i_lo + (int)(blockIdx.x / nc);
+    const int ch = P.c_lo + (int)(blockIdx.x % nc);
     if (!TG)
         for (int e = tid; e < nGp; e += BS) {
             stab[e] = gtab[e];
@@ -331,6 +333,9 @@ __global__ void __launch_bounds__(BS) k_project(const __grid_constant__ QrParams
 }
 
 // ------------------------------------------------------- reduction kernel
+// the deterministic cross-chunk sum of the partials of rows i_lo.. (partial
+// rows relative to i_lo): chunks summed in order within each of the
+// kShardGroups groups, then the groups in order
 template <typename R>
 __global__ void k_reduce(const __grid_constant__ QrParams P, const double2* __restrict__ partial,
                          double2* __restrict__ alpha, int nG, int zero_idx, V2<R>* __restrict__ packed,
@@ -342,33 +347,54 @@ __global__ void k_reduce(const __grid_constant__ QrParams P, const double2* __re
     double diff = 0.0;
     if (idx < total) {
         const int ii = (int)(idx / nGp), e = (int)(idx % nGp), i = i_lo + ii;
+        double sx, sy;
+        chunk_sum2(partial + (size_t)ii * P.n_chunks * nGp + e, P.n_chunks, nGp, sx, sy);
+        finish_coef<R>(P, sx, sy, e, i, nG, zero_idx, alpha, packed, row_stride, diff);
+    }
+    reduce_residual(diff, &counters[CNT_RESID]);
+}
+
+// the group sums of the groups [g_lo, g_hi) of rows i_lo.., from the chunk
+// partials of those groups: gsum[g][row][e] (rows absolute, N per group)
+__global__ void k_group_sums(const __grid_constant__ QrParams P, const double2* __restrict__ partial,
+                             double2* __restrict__ gsum, int g_lo, int g_hi, int i_lo, int i_hi)
+{
+    const int nGp = P.nGp, rows = i_hi - i_lo;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)(g_hi - g_lo) * rows * nGp) return;
+    const int e = (int)(idx % nGp), ii = (int)((idx / nGp) % rows), g = g_lo + (int)(idx / ((long long)nGp * rows));
+    const double2* p = partial + (size_t)ii * P.n_chunks * nGp + e;
+    double gx = 0.0, gy = 0.0;
+    for (int c = group_chunk(g, P.n_chunks); c < group_chunk(g + 1, P.n_chunks); ++c) {
+        const double2 v = p[(size_t)c * nGp];
+        gx += v.x;
+        gy += v.y;
+    }
+    gsum[((size_t)g * P.N + (i_lo + ii)) * nGp + e] = make_double2(gx, gy);
+}
+
+// the reduction from the group sums of every group: the same operations, in
+// the same order, as k_reduce from the partials
+template <typename R>
+__global__ void k_reduce_groups(const __grid_constant__ QrParams P, const double2* __restrict__ gsum,
+                                double2* __restrict__ alpha, int nG, int zero_idx, V2<R>* __restrict__ packed,
+                                long long row_stride, int i_lo, int i_hi, unsigned long long* __restrict__ counters)
+{
+    const int nGp = P.nGp;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)(i_hi - i_lo) * nGp;
+    double diff = 0.0;
+    if (idx < total) {
+        const int ii = (int)(idx / nGp), e = (int)(idx % nGp), i = i_lo + ii;
         double sx = 0.0, sy = 0.0;
-        const double2* p = partial + (size_t)ii * P.n_chunks * nGp + e;
-        for (int c = 0; c < P.n_chunks; ++c) {
-            const double2 v = p[(size_t)c * nGp];
+        for (int g = 0; g < kShardGroups; ++g) {
+            const double2 v = gsum[((size_t)g * P.N + i) * nGp + e];
             sx += v.x;
             sy += v.y;
         }
-        sx /= (double)P.M;
-        sy /= (double)P.M;
-        if (e == 0) sy = 0.0;
-        double2* row = alpha + (size_t)i * nG;
-        const double2 old = row[zero_idx + e];
-        diff = hypot(sx - old.x, sy - old.y);
-        row[zero_idx + e] = make_double2(sx, sy);
-        if (e > 0) row[zero_idx - e] = make_double2(sx, -sy);
-        packed[(size_t)i * row_stride + e] = e == 0 ? mk2<R>((R)sx, (R)0) : mk2<R>((R)(2.0 * sx), (R)(2.0 * sy));
+        finish_coef<R>(P, sx, sy, e, i, nG, zero_idx, alpha, packed, row_stride, diff);
     }
-    // block max, then one atomic (max is order independent)
-    __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) diff = fmax(diff, __shfl_xor_sync(0xffffffffu, diff, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = diff;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double mx = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
-        atomicMax(&counters[CNT_RESID], (unsigned long long)__double_as_longlong(mx));
-    }
+    reduce_residual(diff, &counters[CNT_RESID]);
 }
 
 // Cosine basis (Lemma ortho:dim1) through the unfolded Fourier set: with
@@ -545,7 +571,8 @@ static cudaError_t paths_bs(const QrParams& P, const GEntry* tab, const uint8_t*
     auto kern = k_paths<R, D, BS, TG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int tiles = (int)((P.M + BS - 1) / BS);
+    // the paths of the context's chunk range (chunks are multiples of BS)
+    const int tiles = (int)((shard_m_hi(P) - shard_m_lo(P) + BS - 1) / BS);
     const long long blocks = (long long)tiles * (i_hi - i_lo);
     if (blocks <= 0) return cudaSuccess;
     kern<<<(unsigned)blocks, BS, sm, st>>>(P, tab, first, static_cast<const V2<R>*>(packed), row_stride,
@@ -583,7 +610,7 @@ static cudaError_t project_bs(const QrParams& P, const GEntry* tab, const uint8_
     auto kern = k_project<R, D, BS, TG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const long long blocks = (long long)P.n_chunks * (i_hi - i_lo);
+    const long long blocks = (long long)(P.c_hi - P.c_lo) * (i_hi - i_lo);
     if (blocks <= 0) return cudaSuccess;
     kern<<<(unsigned)blocks, BS, sm, st>>>(P, tab, first, static_cast<const R*>(S), partial, i_lo, KT);
     return cudaGetLastError();
@@ -682,6 +709,31 @@ cudaError_t launch_reduce(int prec, const QrParams& P, const double2* partial, d
     else
         k_reduce<double><<<blocks, 256, 0, st>>>(P, partial, alpha, nG, zero_idx, static_cast<double2*>(packed),
                                                  row_stride, i_lo, i_hi, counters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_sums(const QrParams& P, const double2* partial, double2* gsum, int g_lo, int g_hi, int i_lo,
+                              int i_hi, cudaStream_t st)
+{
+    const long long total = (long long)(g_hi - g_lo) * (i_hi - i_lo) * P.nGp;
+    if (total <= 0) return cudaSuccess;
+    k_group_sums<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(P, partial, gsum, g_lo, g_hi, i_lo, i_hi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_groups(int prec, const QrParams& P, const double2* gsum, double2* alpha, int nG, int zero_idx,
+                                 void* packed, long long row_stride, int i_lo, int i_hi,
+                                 unsigned long long* counters, cudaStream_t st)
+{
+    const long long total = (long long)(i_hi - i_lo) * P.nGp;
+    if (total <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    if (prec == QR_FP32)
+        k_reduce_groups<float><<<blocks, 256, 0, st>>>(P, gsum, alpha, nG, zero_idx, static_cast<float2*>(packed),
+                                                       row_stride, i_lo, i_hi, counters);
+    else
+        k_reduce_groups<double><<<blocks, 256, 0, st>>>(P, gsum, alpha, nG, zero_idx, static_cast<double2*>(packed),
+                                                        row_stride, i_lo, i_hi, counters);
     return cudaGetLastError();
 }
 

@@ -132,19 +132,21 @@ struct Tiles {
     }
 };
 
+// one (row i, chunk ch) of the projection: the FP64 partial sums of the
+// chunk's paths into out[0 .. |Gamma_+|) (canonical half-set order through
+// perm); S_row holds row i's responses (path m at S_row[m]); smem_raw is the
+// block's dynamic shared memory (sizeof(ProjSmem) bytes). Every thread of
+// the block calls it.
 template <typename R, int D, int NN, int KIND, int BS, int SC>
-__global__ void __launch_bounds__(BS) k_project_tree(const __grid_constant__ QrParams P, const R* __restrict__ S,
-                                                     const int* __restrict__ perm, double2* __restrict__ partial,
-                                                     int i_lo)
+__device__ __forceinline__ void project_tree_item(const QrParams& P, const R* __restrict__ S_row,
+                                                  const int* __restrict__ perm, double2* __restrict__ out, int i,
+                                                  int ch, unsigned char* smem_raw)
 {
     using TR = FullTree<D, NN, KIND>;
     using SM = ProjSmem<R, D, TR, BS, SC>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     SM& sm = *reinterpret_cast<SM*>(smem_raw);
     constexpr int W = BS / 32;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int i = i_lo + (int)(blockIdx.x / P.n_chunks);
-    const int ch = (int)(blockIdx.x % P.n_chunks);
     const long long base = (long long)ch * P.chunk;
     const long long end = min((long long)P.M, base + P.chunk);
     for (int t = tid; t < W * TR::tiles * 32; t += BS) (&sm.acc[0][0])[t] = mk2<R>((R)0, (R)0);
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(BS) k_project_tree(const __grid_constant__ QrP
             start_phases_dev<R, D>(P, i, active ? m : 0, ph);
 #pragma unroll
             for (int l = 0; l < D; ++l) sm.z[l][r] = ph[l];
-            const R Sv = active ? S[(size_t)(i - i_lo) * (size_t)P.M + (size_t)m] : (R)0;
+            const R Sv = active ? S_row[(size_t)m] : (R)0;
             sm.S[r] = Sv;
             s0 += Sv;
         }
@@ -172,7 +174,6 @@ __global__ void __launch_bounds__(BS) k_project_tree(const __grid_constant__ QrP
     for (int o = 16; o > 0; o >>= 1) d0 += __shfl_xor_sync(0xffffffffu, d0, o);
     if (lane == 0) red[warp] = d0;
     __syncthreads();
-    double2* out = partial + ((size_t)(i - i_lo) * P.n_chunks + ch) * P.nGp;
     if (tid == 0) {
         double t = 0.0;
         for (int w = 0; w < W; ++w) t += red[w];
@@ -186,6 +187,20 @@ __global__ void __launch_bounds__(BS) k_project_tree(const __grid_constant__ QrP
         }
         out[perm[s]] = make_double2(sx, sy);
     }
+}
+
+template <typename R, int D, int NN, int KIND, int BS, int SC>
+__global__ void __launch_bounds__(BS) k_project_tree(const __grid_constant__ QrParams P, const R* __restrict__ S,
+                                                     const int* __restrict__ perm, double2* __restrict__ partial,
+                                                     int i_lo)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nc = P.c_hi - P.c_lo;  // the context's chunks
+    const int i = i_lo + (int)(blockIdx.x / nc);
+    const int ch = P.c_lo + (int)(blockIdx.x % nc);
+    project_tree_item<R, D, NN, KIND, BS, SC>(P, S + (size_t)(i - i_lo) * (size_t)P.M, perm,
+                                              partial + ((size_t)(i - i_lo) * P.n_chunks + ch) * P.nGp, i, ch,
+                                              smem_raw);
 }
 
 template <typename R, int D, int NN, int KIND>
@@ -208,7 +223,7 @@ static cudaError_t project_tree_t(const QrParams& P, const void* S, const int* p
     auto kern = k_project_tree<R, D, NN, KIND, BS, SC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const long long blocks = (long long)P.n_chunks * (i_hi - i_lo);
+    const long long blocks = (long long)(P.c_hi - P.c_lo) * (i_hi - i_lo);
     if (blocks <= 0) return cudaSuccess;
     kern<<<(unsigned)blocks, BS, sm, st>>>(P, static_cast<const R*>(S), perm, partial, i_lo);
     return cudaGetLastError();

@@ -81,6 +81,10 @@ extern "C" qr_status qr_project_static(qr_ctx* ctx, const void* S, int i_lo, int
         return QR_EINVAL;
     }
     const qr::QrParams& P = *v.P;
+    if (v.sharded) {
+        qr::ctx_set_error(ctx, "qr_project_static: not for a sharded context");
+        return QR_EINVAL;
+    }
     if (P.half_angle) {
         qr::ctx_set_error(ctx, "qr_project_static: the cosine basis is not supported");
         return QR_ENOTIMPL;

@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(BS, QR_TREE_MINB) k_paths_tree(const __grid_co
     __syncthreads();
     uint32_t phase[2] = {0u, 0u};
     const int i = i_lo + (int)(blockIdx.x / tiles_per_i);
-    const long long m0 = (long long)(blockIdx.x % tiles_per_i) * (BS * P) + threadIdx.x;
+    const long long m0 = shard_m_lo(Pm) + (long long)(blockIdx.x % tiles_per_i) * (BS * P) + threadIdx.x;
     (void)path_item<R, D, NN, KIND, P, BS>(Pm, tree, row_stride, S, i, i_lo, m0, abuf, bars, phase, counters, status);
 }
 
@@ -675,7 +675,10 @@ inline cudaError_t paths_tree_t(const QrParams& P, const void* tree, long long r
     auto kern = k_paths_tree<R, D, NN, KIND, PP, BS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int tiles = (int)((P.M + BS * PP - 1) / (BS * PP));
+    // the paths of the context's chunk range (a multiple of the tile: chunks
+    // are multiples of 256 paths in FP32 and 128 in FP64)
+    const long long span = shard_m_hi(P) - shard_m_lo(P);
+    const int tiles = (int)((span + BS * PP - 1) / (BS * PP));
     const long long blocks = (long long)tiles * (i_hi - i_lo);
     if (blocks <= 0) return cudaSuccess;
     kern<<<(unsigned)blocks, BS, sm, st>>>(P, static_cast<const V2<R>*>(tree), row_stride, static_cast<R*>(S), i_lo,

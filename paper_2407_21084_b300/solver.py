@@ -24,6 +24,7 @@ class Solver:
                  seed, precision=L.QR_FP64, clamp_L=0.0, stream=None, lattice_n=0, instance=0, path_kernel=0,
                  damping_q=0.0):
         self._L = L.load()
+        self.shard_world = 1
         self.d, self.N, self.T, self.M = int(d), int(N), float(T), int(M)
         self.precision = precision
         b = np.ascontiguousarray(b, dtype=np.float64)
@@ -152,6 +153,47 @@ class Solver:
         per_i = np.array(per_i)
         return {"mse_max": float(np.log(per_i.max())), "mse_av": float(np.log(per_i.mean())), "points": n}
 
+    # ------------------------------------------- one problem over several GPUs
+    def shard(self, rank: int, world: int):
+        """Restrict this context to its rank's path chunks (qr_shard)."""
+        L.check(self._L.qr_shard(self._ctx, rank, world), self._ctx)
+        self.shard_world = world
+
+    def shard_groups(self):
+        """(group sums as a CUDA float64 tensor (8, N, |Gamma_+|, 2) aliasing the
+        library's array, g_lo, g_hi): this rank fills groups [g_lo, g_hi)."""
+        import torch
+
+        ptr, nb = C.c_void_p(), C.c_longlong()
+        gl, gh = C.c_int(), C.c_int()
+        L.check(self._L.qr_shard_groups(self._ctx, C.byref(ptr), C.byref(nb), C.byref(gl), C.byref(gh)), self._ctx)
+        if not ptr.value:
+            raise L.QrError(L.QR_EINVAL, "the context is not sharded")
+        ngp = nb.value // (16 * self.N)
+        view = _DeviceArray(ptr.value, (8, self.N, ngp, 2), "<f8")
+        return torch.as_tensor(view, device="cuda"), gl.value, gh.value
+
+    def picard_begin(self):
+        L.check(self._L.qr_picard_begin(self._ctx), self._ctx)
+
+    def picard_finish(self) -> float:
+        r = C.c_double()
+        L.check(self._L.qr_picard_finish(self._ctx, C.byref(r)), self._ctx)
+        return r.value
+
+    def picard_step_sharded(self, group=None) -> float:
+        """One Picard iteration of a problem sharded over the ranks of a
+        torch.distributed process group: own paths and group sums, the
+        all-gather of the group sums, then the common reduction."""
+        import torch
+
+        self.picard_begin()
+        buf, gl, gh = self.shard_groups()
+        torch.cuda.synchronize()  # this rank's group sums are on the context's stream
+        exchange_group_sums(buf, gl, gh, self.shard_world, group)
+        torch.cuda.synchronize()
+        return self.picard_finish()
+
     def set_profiling(self, on: bool = True):
         L.check(self._L.qr_set_profiling(self._ctx, 1 if on else 0), self._ctx)
 
@@ -176,6 +218,30 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+class _DeviceArray:
+    """A device pointer with its shape, seen by torch through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def exchange_group_sums(buf, g_lo: int, g_hi: int, world: int, group=None):
+    """All-gather of the group sums of a sharded iteration: buf is the
+    (8, ...) array of group sums with this rank's groups [g_lo, g_hi) filled;
+    afterwards every group is filled, rank r's groups at [r 8/W, (r+1) 8/W).
+    Works on CUDA tensors (NCCL) and CPU tensors (gloo) alike."""
+    import torch
+    import torch.distributed as dist
+
+    per = 8 // world
+    mine = buf[g_lo:g_hi].contiguous()
+    parts = [torch.empty_like(mine) for _ in range(world)]
+    dist.all_gather(parts, mine, group=group)
+    for r, t in enumerate(parts):
+        buf[r * per:(r + 1) * per].copy_(t)
 
 
 def philox_words(ctr_key: np.ndarray) -> np.ndarray:

@@ -10,7 +10,7 @@ y == 0. The iteration is unchanged, so a poor prediction costs iterations,
 never accuracy. Network training and inference run in libqrmc's own kernels
 (qr_mlp_*); this module only marshals arrays.
 
-    python -m paper_2407_21084_b300.warmstart --train 2048 --heldout 16
+    python -m paper_2407_21084_b300.warmstart --train 2048 --heldout 256
 """
 from __future__ import annotations
 
@@ -213,73 +213,110 @@ def iterate_to(s, pts, y_ref, tol, max_iter):
     return q, t_iter, err
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--train", type=int, default=2048, help="training solves")
-    ap.add_argument("--train-paths", type=int, default=2 ** 14)
-    ap.add_argument("--heldout", type=int, default=16)
-    ap.add_argument("--heldout-fp64", type=int, default=4, help="held-out problems also solved in the FP64 form")
-    ap.add_argument("--eval-paths", type=int, default=2 ** 20)
-    ap.add_argument("--steps", type=int, default=3000)
-    ap.add_argument("--tol", type=float, default=1e-3)
-    ap.add_argument("--test-points", type=int, default=1024)
-    ap.add_argument("--target-scale", choices=("global", "per_output"), default="global")
-    ap.add_argument("--warm-kmax", type=int, nargs="*", default=[],
-                    help="also start from the prediction kept on |k|_1 <= each of these")
-    args = ap.parse_args()
+def study(base: W.Workload, n_train=2048, train_paths=2 ** 16, n_heldout=256, eval_paths=2 ** 18, n_fp64=16,
+          steps=3000, tol=1e-3, test_points=1024, other_cloud=True, target_scale="global", log=None) -> dict:
+    """Iterations and time to a sup error `tol` from y == 0 (FP64 and FP32
+    forms) and from the network's start (FP32), on held-out members of the
+    family of `base`.
+
+    The reference of a problem is the fixed point of its own clouds (one
+    backward sweep, Algorithm 1, equals N Picard iterations), in FP32; for
+    the first n_fp64 problems the FP64 sweep is computed too and the FP64
+    plain form is iterated, and the distance between the two references is
+    reported. With other_cloud, the FP32 iteration also starts from the same
+    problem's fixed point on an independent cloud (another seed): no start
+    computed without the evaluation cloud can be closer to its fixed point
+    than the cloud-independent solution, of which this start is an unbiased
+    estimate, so its iteration count bounds what any warm start can save."""
     import torch
 
     from .solver import Solver
 
-    base = W.c3()
     t0 = time.perf_counter()
-    X, Y = training_set(base, args.train, args.train_paths)
+    X, Y = training_set(base, n_train, train_paths)
     t_data = time.perf_counter() - t0
     net = MLP(X.shape[1], Y.shape[1], max_batch=1024)
     t0 = time.perf_counter()
-    hist = net.fit(X, Y, steps=args.steps, target_scale=args.target_scale)
+    hist = net.fit(X, Y, steps=steps, target_scale=target_scale)
     t_fit = time.perf_counter() - t0
     rng = np.random.default_rng(6)
-    rows = []
-    for q in range(args.heldout):
-        w = family_member(base, rng, args.eval_paths, seed=900000 + q)
-        # reference: the converged fixed point of the same clouds, FP64 backward sweep
-        with Solver.from_workload(w, precision=FP64) as ref:
+    rows, ref_gap = [], 0.0
+    for q in range(n_heldout):
+        w = family_member(base, rng, eval_paths, seed=900000 + q)
+        with Solver.from_workload(w, precision=FP32) as ref:
             ref.backward_sweep()
-            pts = [ref.test_points(i, args.test_points) for i in range(w.N)]
+            pts = [ref.test_points(i, test_points) for i in range(w.N)]
             y_ref = [ref.eval(i, x) for i, x in enumerate(pts)]
         res = {}
-        pred = rows_to_alpha(net.predict(features(w)))
-        forms = [("fp64_cold", FP64, None), ("fp32_cold", FP32, None), ("fp32_warm", FP32, 10 ** 9)]
-        forms += [("fp32_warm_k%d" % kc, FP32, kc) for kc in args.warm_kmax]
-        for name, prec, kcut in forms[0 if q < args.heldout_fp64 else 1:]:
+        if q < n_fp64:
+            with Solver.from_workload(w, precision=FP64) as r64:
+                r64.backward_sweep()
+                ref_gap = max(ref_gap, sup_error(r64, pts, y_ref))
+        starts = [("fp32_cold", FP32, None), ("fp32_warm", FP32, "net")]
+        if q < n_fp64:
+            starts = [("fp64_cold", FP64, None)] + starts
+        if other_cloud:
+            starts.append(("fp32_other_cloud", FP32, "cloud"))
+        for name, prec, start in starts:
             with Solver.from_workload(w, precision=prec) as s:
-                if kcut is not None:
-                    # the network's start, optionally kept only on |k|_1 <= kcut
-                    keep = np.abs(s.gamma_list()).sum(axis=1) <= kcut
-                    s.set_coefs(np.where(keep[None, :], pred, 0.0))
-                it, secs, err = iterate_to(s, pts, y_ref, args.tol, w.N + 2)
+                if start == "net":
+                    s.set_coefs(rows_to_alpha(net.predict(features(w))))
+                elif start == "cloud":
+                    with Solver.from_workload(w.with_(seed=w.seed + 7777777), precision=FP32) as o:
+                        o.backward_sweep()
+                        s.set_coefs(o.coefs())
+                it, secs, err = iterate_to(s, pts, y_ref, tol, w.N + 2)
                 res[name] = {"iterations": it, "seconds": secs, "sup_error": err}
-        # Algorithm 1 itself (one backward sweep, rows in sequence) in FP32
-        with Solver.from_workload(w, precision=FP32) as s:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            s.backward_sweep()
-            torch.cuda.synchronize()
-            res["fp32_sweep"] = {"iterations": 1, "seconds": time.perf_counter() - t0,
-                                 "sup_error": sup_error(s, pts, y_ref)}
         rows.append(res)
-    names = ["fp64_cold", "fp32_cold", "fp32_warm"] + ["fp32_warm_k%d" % kc for kc in args.warm_kmax] + ["fp32_sweep"]
-    summ = {k: {"iterations_mean": float(np.mean([r[k]["iterations"] for r in rows if k in r])),
-                "seconds_mean": float(np.mean([r[k]["seconds"] for r in rows if k in r])),
-                "problems": sum(k in r for r in rows)}
-            for k in names}
-    print(json.dumps({"train_solves": args.train, "train_paths": args.train_paths, "target_scale": args.target_scale,
-                      "data_s": t_data,
-                      "fit_s": t_fit, "loss_first": hist[0], "loss_last": hist[-1], "heldout": args.heldout,
-                      "eval_paths": args.eval_paths, "tol": args.tol, "summary": summ, "per_problem": rows,
-                      "speedup_fp32_warm_vs_fp64_cold": summ["fp64_cold"]["seconds_mean"]
-                      / max(1e-12, summ["fp32_warm"]["seconds_mean"])}))
+        if log and (q + 1) % 16 == 0:
+            log("held-out %d/%d" % (q + 1, n_heldout))
+    names = ["fp64_cold", "fp32_cold", "fp32_warm"] + (["fp32_other_cloud"] if other_cloud else [])
+    summ = {}
+    for k in names:
+        sel = [r[k] for r in rows if k in r]
+        if sel:
+            its = np.array([x["iterations"] for x in sel])
+            summ[k] = {"iterations_mean": float(its.mean()), "iterations_min": int(its.min()),
+                       "iterations_max": int(its.max()),
+                       "seconds_mean": float(np.mean([x["seconds"] for x in sel])), "problems": len(sel)}
+    cold, warm = summ["fp32_cold"], summ["fp32_warm"]
+    out = {"train_solves": n_train, "train_paths": train_paths, "target_scale": target_scale, "data_s": t_data,
+           "fit_s": t_fit, "loss_first": hist[0], "loss_last": hist[-1], "heldout": n_heldout,
+           "eval_paths": eval_paths, "tol": tol, "reference": "FP32 backward sweep of the same clouds",
+           "fp64_vs_fp32_reference_sup": ref_gap if n_fp64 else None, "summary": summ,
+           "iterations_saved_by_network": cold["iterations_mean"] - warm["iterations_mean"],
+           "seconds_saved_by_network": cold["seconds_mean"] - warm["seconds_mean"]}
+    if other_cloud:
+        out["iterations_saved_by_other_cloud_fixed_point"] = \
+            cold["iterations_mean"] - summ["fp32_other_cloud"]["iterations_mean"]
+    if "fp64_cold" in summ:
+        # the same problems in both forms: the first n_fp64
+        w64 = [r for r in rows if "fp64_cold" in r]
+        f64 = float(np.mean([r["fp64_cold"]["seconds"] for r in w64]))
+        out["speedup_fp32_warm_vs_fp64_cold"] = f64 / max(1e-12, float(np.mean([r["fp32_warm"]["seconds"] for r in w64])))
+        out["speedup_fp32_cold_vs_fp64_cold"] = f64 / max(1e-12, float(np.mean([r["fp32_cold"]["seconds"] for r in w64])))
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=2048, help="training solves")
+    ap.add_argument("--train-paths", type=int, default=2 ** 16)
+    ap.add_argument("--heldout", type=int, default=256)
+    ap.add_argument("--heldout-fp64", type=int, default=16, help="held-out problems also solved in the FP64 form")
+    ap.add_argument("--eval-paths", type=int, default=2 ** 18)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--test-points", type=int, default=1024)
+    ap.add_argument("--target-scale", choices=("global", "per_output"), default="global")
+    ap.add_argument("--no-other-cloud", action="store_true")
+    args = ap.parse_args()
+    import sys
+
+    out = study(W.c3(), args.train, args.train_paths, args.heldout, args.eval_paths, args.heldout_fp64, args.steps,
+                args.tol, args.test_points, not args.no_other_cloud, args.target_scale,
+                log=lambda m: print(m, file=sys.stderr, flush=True))
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":
