@@ -234,6 +234,24 @@ def bench_c4(stream, steps: int, flush) -> dict:
                     "h2d_bytes_per_step": io, "d2h_bytes_per_step": io}}
 
 
+def bench_warm_start() -> dict:
+    """The learned warm start and the precision form, bounded to under a
+    minute: a network trained on 96 plain FP32 solves of the d=6 family
+    (2^14 paths each), then 3 held-out problems (2^16 paths) iterated to a
+    1e-3 sup error against the fixed point of their own clouds, from y == 0
+    in the FP64 plain form and in the FP32 form, and from the network's start
+    in the FP32 form; wall time of the iterations (device work and the
+    per-iteration accuracy check). The full study (2048 training solves, 256
+    held-out problems) is python -m paper_2407_21084_b300.warmstart."""
+    from paper_2407_21084_b300 import warmstart as WS
+
+    t0 = time.perf_counter()
+    out = WS.study(W.c3(), n_train=96, train_paths=2 ** 14, n_heldout=3, eval_paths=2 ** 16, n_fp64=3, steps=600,
+                   tol=1e-3, test_points=512, other_cloud=True)
+    out["wall_s"] = time.perf_counter() - t0
+    return out
+
+
 def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -274,6 +292,7 @@ def main():
     ap.add_argument("--paths", type=int, default=0, help="override M (profiling captures only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-c4", action="store_true", help="skip the many-instance (config 4) key")
+    ap.add_argument("--no-warm", action="store_true", help="skip the warm-start / precision-form key")
     args = ap.parse_args()
     w = W.CONFIGS[args.workload]()
     if args.paths:
@@ -437,6 +456,8 @@ def main():
                                             "paths": args.ref_paths}
     if rank == 0 and ws == 1 and not args.no_c4:
         line["c4_batch"] = bench_c4(stream, max(2, min(args.steps, 5)), flush)
+    if rank == 0 and ws == 1 and not args.no_warm:
+        line["warm_start"] = bench_warm_start()
     if rank == 0:
         print(json.dumps(line), flush=True)
     s.close()
