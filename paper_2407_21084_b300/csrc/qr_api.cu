@@ -239,9 +239,10 @@ bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vect
     return ok && emitted == (nG - 1) / 2;
 }
 
-// Order of the half set in the tiled projection (mirrors qr_proj_tree.cu):
-// depth-first along the chain tree with both signs of every new dimension
-// expanded; perm[s] = canonical half-set index (>= 1) of the s-th node.
+// Order of the half set in the tiled projection (mirrors FullTree of
+// qr_ptree.cuh): depth-first along the chain tree with both signs of every
+// new dimension expanded, the +- chains of the last dimension interleaved
+// (+1, -1, +2, -2, ...); perm[s] = canonical half-set index (>= 1) of node s.
 bool build_proj_perm(int kind, int d, int n, const std::vector<int>& K, int zero_idx, std::vector<int>& perm)
 {
     const int nG = (int)(K.size() / d);
@@ -266,11 +267,25 @@ bool build_proj_perm(int kind, int d, int n, const std::vector<int>& K, int zero
         }
         if (l1 ? S >= 1 : true)
             for (int l2 = L + 1; l2 < d; ++l2) {
+                const int S2 = l1 ? S - 1 : 1;
+                if (l2 == d - 1) {
+                    int len = 1;
+                    for (int t = S2; l1 ? t >= 1 : t < n; t = l1 ? t - 1 : t + 1) ++len;
+                    for (int m = 1; m <= len; ++m)
+                        for (int sg : {+1, -1}) {
+                            std::vector<int> km = k;
+                            km[l2] += sg * m;
+                            const int e = find(km);
+                            if (e <= zero_idx) ok = false;
+                            perm.push_back(e - zero_idx);
+                        }
+                    continue;
+                }
                 std::vector<int> kp = k, km = k;
                 kp[l2] += 1;
                 km[l2] -= 1;
-                visit(l2, l1 ? S - 1 : 1, kp);
-                visit(l2, l1 ? S - 1 : 1, km);
+                visit(l2, S2, kp);
+                visit(l2, S2, km);
             }
     };
     for (int l = 0; l < d; ++l) {

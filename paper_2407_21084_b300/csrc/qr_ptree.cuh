@@ -11,28 +11,63 @@ namespace qr {
 template <int D, int NN, int KIND>
 struct FullTree {
     static constexpr int kMax = 2048;
+    // node s: basis value = basis of parent[s] times z_dim^sgn. A mirrored
+    // pair s, s+1 (pairnext[s]) are k' + m e_dim and k' - m e_dim for the
+    // frame node k' = frame[s] (-1: the root) and the power m = pw[s]: the
+    // projection accumulates S conj(phi) of both from S conj(phi_frame) and
+    // z_dim^m with 8 FMA.
     struct Nodes {
         int n = 0;
         signed char dim[kMax] = {};
         signed char sgn[kMax] = {};
         short parent[kMax] = {};
+        short frame[kMax] = {};
+        signed char pw[kMax] = {};
+        bool pairnext[kMax] = {};
     };
     static constexpr bool ext_ok(int S) { return KIND == QR_G_L1 ? S >= 1 : S < NN; }
     static constexpr int ext_S(int S) { return KIND == QR_G_L1 ? S - 1 : S + 1; }
     static constexpr bool new_ok(int S) { return KIND == QR_G_L1 ? S >= 1 : true; }
     static constexpr int new_S(int S) { return KIND == QR_G_L1 ? S - 1 : 1; }
-    // node reached by multiplying its parent's basis by z_dim^sgn, in state S
-    static constexpr void visit(Nodes& t, int L, int S, int parent, int sgn)
+    // nodes of a last-dimension node in state S and its chain of extensions
+    static constexpr int chain_len(int S) { return 1 + (ext_ok(S) ? chain_len(ext_S(S)) : 0); }
+    static constexpr int add(Nodes& t, int L, int parent, int sgn)
     {
         const int me = t.n++;
         t.dim[me] = (signed char)L;
         t.sgn[me] = (signed char)sgn;
         t.parent[me] = (short)parent;
+        t.frame[me] = -1;
+        return me;
+    }
+    // node reached by multiplying its parent's basis by z_dim^sgn, in state S;
+    // the +- chains of the last dimension are interleaved (+1, -1, +2, -2, ...)
+    static constexpr void visit(Nodes& t, int L, int S, int parent, int sgn)
+    {
+        const int me = add(t, L, parent, sgn);
         if (ext_ok(S)) visit(t, L, ext_S(S), me, sgn);
         if (new_ok(S))
             for (int l2 = L + 1; l2 < D; ++l2) {
-                visit(t, l2, new_S(S), me, +1);
-                visit(t, l2, new_S(S), me, -1);
+                const int S2 = new_S(S);
+                if (l2 == D - 1) {
+                    int pp = me, pm = me;
+                    for (int m = 1; m <= chain_len(S2); ++m) {
+                        pp = add(t, l2, pp, +1);
+                        pm = add(t, l2, pm, -1);
+                        t.frame[pp] = t.frame[pm] = (short)me;
+                        t.pw[pp] = t.pw[pm] = (signed char)m;
+                        t.pairnext[pp] = true;
+                    }
+                } else if (!ext_ok(S2) && !new_ok(S2)) {
+                    // a +-1 pair of leaves in dimension l2
+                    const int a = add(t, l2, me, +1), b = add(t, l2, me, -1);
+                    t.frame[a] = t.frame[b] = (short)me;
+                    t.pw[a] = t.pw[b] = 1;
+                    t.pairnext[a] = true;
+                } else {
+                    visit(t, l2, S2, me, +1);
+                    visit(t, l2, S2, me, -1);
+                }
             }
     }
     static constexpr Nodes build()
@@ -45,6 +80,17 @@ struct FullTree {
     static constexpr Nodes nodes = build();
     static constexpr int n = nodes.n;  // |Gamma_+| without k = 0
     static constexpr int tiles = (n + 31) / 32;
+    // whether node s is the + member of a mirrored pair that tile layout keeps
+    // together (both within one tile of 32)
+    static constexpr bool pair_at(int s) { return nodes.pairnext[s] && (s % 32) != 31 && s + 1 < n; }
+    // highest power of the last dimension's phase that tile T's pairs use
+    static constexpr int tile_pow(int T)
+    {
+        int m = 1;
+        for (int s = T * 32; s < T * 32 + 32 && s < n; ++s)
+            if (pair_at(s) && nodes.dim[s] == D - 1 && nodes.pw[s] > m) m = nodes.pw[s];
+        return m;
+    }
 };
 
 // basis value of node s (prefix products are shared by common subexpressions)
@@ -62,15 +108,39 @@ __device__ __forceinline__ V2<R> bval(const V2<R> (&z)[D])
         return cmul<R>(bval<R, D, TR, p>(z), w);
 }
 
-template <typename R, int D, class TR, int T, int j>
+template <typename R, int D, class TR, int T, int j, int NP>
 struct TileSlots {
-    static __device__ __forceinline__ void run(const V2<R> (&z)[D], R S, V2<R> (&acc)[32])
+    // zl[m-1] = z[D-1]^m
+    static __device__ __forceinline__ void run(const V2<R> (&z)[D], const V2<R> (&zl)[NP], R S, V2<R> (&acc)[32])
     {
-        if constexpr (j < 32 && T * 32 + j < TR::n) {
-            const V2<R> b = bval<R, D, TR, T * 32 + j>(z);
-            acc[j].x = fma(S, b.x, acc[j].x);
-            acc[j].y = fma(-S, b.y, acc[j].y);  // S conj(phi_k)
-            TileSlots<R, D, TR, T, j + 1>::run(z, S, acc);
+        constexpr int s = T * 32 + j;
+        if constexpr (j < 32 && s < TR::n) {
+            if constexpr (TR::pair_at(s)) {
+                // k' +- m e_l: with w = S conj(phi_k') and z_l^m = (a, b),
+                // S conj(phi_{k'+m e}) = w conj(z^m), S conj(phi_{k'-m e}) = w z^m
+                constexpr int f = TR::nodes.frame[s], dm = TR::nodes.dim[s], m = TR::nodes.pw[s];
+                R p = S, q = (R)0;
+                if constexpr (f >= 0) {
+                    const V2<R> b = bval<R, D, TR, f>(z);
+                    p = S * b.x;
+                    q = -S * b.y;
+                }
+                V2<R> zm;
+                if constexpr (m == 1)
+                    zm = z[dm];
+                else
+                    zm = zl[m - 1];
+                acc[j].x = fma(p, zm.x, fma(q, zm.y, acc[j].x));
+                acc[j].y = fma(q, zm.x, fma(-p, zm.y, acc[j].y));
+                acc[j + 1].x = fma(p, zm.x, fma(-q, zm.y, acc[j + 1].x));
+                acc[j + 1].y = fma(q, zm.x, fma(p, zm.y, acc[j + 1].y));
+                TileSlots<R, D, TR, T, j + 2, NP>::run(z, zl, S, acc);
+            } else {
+                const V2<R> b = bval<R, D, TR, s>(z);
+                acc[j].x = fma(S, b.x, acc[j].x);
+                acc[j].y = fma(-S, b.y, acc[j].y);  // S conj(phi_k)
+                TileSlots<R, D, TR, T, j + 1, NP>::run(z, zl, S, acc);
+            }
         }
     }
 };
@@ -115,7 +185,12 @@ struct Tiles {
                 V2<R> z[D];
 #pragma unroll
                 for (int l = 0; l < D; ++l) z[l] = sm.z[l][pth];
-                TileSlots<R, D, TR, T, 0>::run(z, sm.S[pth], acc);
+                constexpr int NP = TR::tile_pow(T);
+                V2<R> zl[NP];
+                zl[0] = z[D - 1];
+#pragma unroll
+                for (int mm = 1; mm < NP; ++mm) zl[mm] = cmul<R>(zl[mm - 1], z[D - 1]);
+                TileSlots<R, D, TR, T, 0, NP>::run(z, zl, sm.S[pth], acc);
             }
             R vr[32], vi[32];
 #pragma unroll
