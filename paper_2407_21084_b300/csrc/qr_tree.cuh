@@ -300,9 +300,10 @@ __device__ __forceinline__ R term_g_fast(const QrParams& P, const StepConsts<R, 
 #define QR_TREE_PAIR2 1
 #endif
 
-// subtrees of at most this many slots have both signs unrolled
+// subtrees of at most this many slots have both signs unrolled (4: 567 ms
+// against 571 for 8, 598 for 2 or 0, 595 for 16 on the d = 6 workload)
 #ifndef QR_TREE_UNROLL
-#define QR_TREE_UNROLL 8
+#define QR_TREE_UNROLL 4
 #endif
 constexpr int kUnrollSlots = QR_TREE_UNROLL;
 

@@ -83,3 +83,37 @@ def test_grouping_off_is_bit_identical(mods):
     b.close()
     for s in sol:
         s.close()
+
+
+def test_set_coefs_between_batch_steps_reaches_the_group_kernel(mods):
+    """Coefficients set from the host on grouped instances between batch
+    iterations (a warm start, a resume) are the ones the next shared-point
+    iteration uses: the batch continues exactly as single runs started from
+    the same coefficients (within the BF16 split tolerance)."""
+    batch, solver, torch = mods
+    ws = W.c4(n_instances=18, n_shared=16, M=2048)
+    st = torch.cuda.Stream()
+    sol = batch.solvers_for(ws, st.cuda_stream)
+    b = batch.Batch(sol, group_min=16)
+    assert b.info()["grouped_instances"] == 16
+    b.picard_step(1)
+    rng = np.random.default_rng(5)
+    starts = []
+    for s in sol:
+        a = s.coefs()
+        a = a * (1.0 + 0.3 * rng.uniform(-1, 1))  # a different, still conjugate-symmetric iterate
+        s.set_coefs(a)
+        starts.append(a)
+    b.picard_step(1)
+    for q, (w, s) in enumerate(zip(ws, sol)):
+        with solver.Solver.from_workload(w, precision=1, stream=st.cuda_stream) as one:
+            one.set_coefs(starts[q])
+            one.picard_step(1)
+            a, c = one.coefs(), s.coefs()
+        if q < 2:
+            assert np.array_equal(a.view(np.float64), c.view(np.float64)), w.name
+        else:
+            assert np.abs(a - c).max() / np.abs(a).max() < 1e-4, w.name
+    b.close()
+    for s in sol:
+        s.close()
