@@ -26,8 +26,9 @@
  *    recorded in the context and returned by the call that launched the
  *    work; qr_last_error() gives a text.
  *  - The caller owns every array it passes. The context owns its device
- *    buffers (allocated with cudaMallocAsync on the context's stream at
- *    qr_init, freed by qr_destroy).
+ *    buffers (allocated at qr_init, freed by qr_destroy, on the context's
+ *    stream: by the caller's allocator when qr_opts gives one, else by
+ *    cudaMallocAsync / cudaFreeAsync).
  *  - A context is not thread-safe; distinct contexts are independent.
  *  - Host arrays are plain C arrays; "device" arrays are CUDA device
  *    pointers of the current device.
@@ -44,6 +45,7 @@
 #ifndef QR_H
 #define QR_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -163,6 +165,18 @@ typedef struct {
                                  is multiplied by the weight before T_L and f, the
                                  response divided by the weight at X_i^i); qr_eval
                                  returns ybar^q. A QR_GT_TRIGPOLY g stays undamped. */
+    /* Device memory of the context (and of a batch built on it): when both
+     * are set, every device buffer the context owns is obtained by
+     * dev_alloc(bytes, stream, alloc_user) and returned by
+     * dev_free(ptr, stream, alloc_user), stream being the context's stream
+     * (all use of the buffer is ordered on it); dev_alloc returns NULL on
+     * failure (qr_init then fails with QR_ENOMEM). Both NULL (the default):
+     * cudaMallocAsync / cudaFreeAsync on the context's stream. A caller
+     * running under another allocator (a framework's caching allocator, a
+     * fixed pool) passes its own pair; the Python binding passes PyTorch's. */
+    void* (*dev_alloc)(size_t bytes, void* stream, void* alloc_user);
+    void (*dev_free)(void* ptr, void* stream, void* alloc_user);
+    void* alloc_user;
 } qr_opts;
 
 /* Creates a context: validates the problem, enumerates Gamma, allocates the
@@ -246,9 +260,14 @@ qr_status qr_selftest_wait_timeout(qr_ctx* ctx);
  * d = 2; |k|_1 <= 5 (d = 3), 4 (d = 4, 5, 6), 3 (d = 6, 7, 8)) by Picard
  * iterations together. The path-and-series phase of all instances is one
  * persistent kernel launch pulling (instance, time index, path tiles) work
- * items, class by class and longest first within a class; projection and
- * reduction follow per instance; one
- * iteration is one CUDA graph launch. The first qr_batch_picard_step times a
+ * items, class by class and longest first within a class; instances that
+ * share their sample points run the tensor-core kernel below; then ONE
+ * finishing launch projects every (instance, row, chunk of paths), and the
+ * last chunk of each row to finish reduces it (the same fixed-order sum as
+ * qr_picard_step, so an instance on the persistent kernel ends with its single
+ * run's coefficients bit for bit) and repacks its working rows. One iteration is one CUDA graph
+ * launch of three kernels. Coefficients set with qr_set_coefs between batch
+ * iterations are picked up by the next one. The first qr_batch_picard_step times a
  * few item sizes and grids and keeps the fastest (autotuning). The batch
  * does not own the contexts: destroy it before them. Results per instance
  * are read with qr_get_coefs etc. max_residual (nullable): the largest

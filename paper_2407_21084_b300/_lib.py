@@ -60,7 +60,43 @@ class QrOpts(C.Structure):
         ("instance", C.c_int),
         ("path_kernel", C.c_int),
         ("damping_q", C.c_double),
+        ("dev_alloc", C.c_void_p),
+        ("dev_free", C.c_void_p),
+        ("alloc_user", C.c_void_p),
     ]
+
+
+# device allocator callbacks of qr_opts (dev_alloc / dev_free)
+DEV_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+DEV_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+def _torch_alloc(nbytes, stream, user):
+    try:
+        import torch
+
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+    except Exception:  # noqa: BLE001  (the library reports QR_ENOMEM)
+        return None
+
+
+def _torch_free(ptr, stream, user):
+    try:
+        import torch
+
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:  # noqa: BLE001  (interpreter shutdown: the memory goes with the process)
+        pass
+
+
+TORCH_ALLOC = DEV_ALLOC(_torch_alloc)
+TORCH_FREE = DEV_FREE(_torch_free)
+
+
+def torch_allocator():
+    """(dev_alloc, dev_free) pointers for qr_opts: PyTorch's caching allocator
+    on the context's stream."""
+    return C.cast(TORCH_ALLOC, C.c_void_p), C.cast(TORCH_FREE, C.c_void_p)
 
 
 class QrStats(C.Structure):

@@ -50,6 +50,10 @@ struct qr_ctx {
     // one problem sharded over ranks by path chunks (qr_shard): this
     // context's rank and world size, and the group sums exchanged per iteration
     int shard_rank = 0, shard_world = 1;
+    // the caller's device allocator (qr_opts), NULL: cudaMallocAsync
+    void* (*dev_alloc)(size_t, void*, void*) = nullptr;
+    void (*dev_free)(void*, void*, void*) = nullptr;
+    void* alloc_user = nullptr;
     bool coefs_changed = true;  // by qr_set_coefs since a batch last packed its group blocks
     double2* d_gsum = nullptr;  // kShardGroups x N x |Gamma_+|
     // cosine basis on N^d (Lemma ortho:dim1), run as the unfolded Z^d set
@@ -298,12 +302,33 @@ bool build_proj_perm(int kind, int d, int n, const std::vector<int>& K, int zero
     return ok && (int)perm.size() == (nG - 1) / 2 && std::unique(seen.begin(), seen.end()) == seen.end();
 }
 
+// device memory of a context: the caller's allocator when it gave one, else
+// stream-ordered allocation on the context's stream
+void* ctx_malloc(qr_ctx* c, size_t bytes)
+{
+    bytes = bytes < 16 ? 16 : bytes;
+    if (c->dev_alloc) return c->dev_alloc(bytes, c->stream, c->alloc_user);
+    void* q = nullptr;
+    return cudaMallocAsync(&q, bytes, c->stream) == cudaSuccess ? q : nullptr;
+}
+
+void ctx_free(qr_ctx* c, void* p)
+{
+    if (!p) return;
+    if (c->dev_free)
+        c->dev_free(p, c->stream, c->alloc_user);
+    else
+        cudaFreeAsync(p, c->stream);
+}
+
 template <typename T>
 qr_status dalloc(qr_ctx* c, T** p, size_t bytes)
 {
-    void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, bytes < 16 ? 16 : bytes, c->stream);
-    if (e != cudaSuccess) return fail(c, QR_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+    void* q = ctx_malloc(c, bytes);
+    if (!q) {
+        cudaGetLastError();
+        return fail(c, QR_ENOMEM, "device allocation failed (" + std::to_string(bytes) + " bytes)");
+    }
     *p = static_cast<T*>(q);
     return QR_OK;
 }
@@ -316,8 +341,8 @@ void release(qr_ctx* c)
                         c->d_partial, c->d_counters, c->d_status,   c->d_tree,      c->d_tmap,
                         c->d_perm,    c->d_alpha_raw, c->d_orb_off, c->d_orb_idx, c->d_cgroups,
                         c->d_cflags,  c->d_cpos,     c->d_gsum};
-        for (void* p : ptrs)
-            if (p) cudaFreeAsync(p, c->stream);
+        cudaStreamSynchronize(c->stream);  // nothing of the context in flight
+        for (void* p : ptrs) ctx_free(c, p);
         cudaStreamSynchronize(c->stream);
     }
     if (c->h_counters) cudaFreeHost(c->h_counters);
@@ -777,6 +802,10 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     P.c_hi = P.n_chunks;
 
     // device state
+    if (!o.dev_alloc != !o.dev_free) return bail(QR_EINVAL, "dev_alloc and dev_free go together");
+    c->dev_alloc = o.dev_alloc;
+    c->dev_free = o.dev_free;
+    c->alloc_user = o.alloc_user;
     QR_CU(c, cudaGetDevice(&c->device));
     if (o.stream) {
         c->stream = static_cast<cudaStream_t>(o.stream);
@@ -1116,7 +1145,8 @@ qr_status qr_eval(qr_ctx* ctx, int i, const double* x, long long n, double* y_ou
     double* dy = y_out;
     double* tmp = nullptr;
     if (ptr_kind == QR_HOST) {
-        QR_CU(ctx, cudaMallocAsync(&tmp, sizeof(double) * (size_t)n * (ctx->d + 1), ctx->stream));
+        tmp = static_cast<double*>(ctx_malloc(ctx, sizeof(double) * (size_t)n * (ctx->d + 1)));
+        if (!tmp) return fail(ctx, QR_ENOMEM, "qr_eval: device allocation failed");
         QR_CU(ctx, cudaMemcpyAsync(tmp, x, sizeof(double) * (size_t)n * ctx->d, cudaMemcpyHostToDevice, ctx->stream));
         dx = tmp;
         dy = tmp + (size_t)n * ctx->d;
@@ -1128,12 +1158,13 @@ qr_status qr_eval(qr_ctx* ctx, int i, const double* x, long long n, double* y_ou
                                           ctx->stream)
                         : launch_eval(ctx->prec, ctx->P, ctx->d_tab, ctx->d_first, row, dx, n, dy, use_g, ctx->stream);
     if (e != cudaSuccess) {
-        if (tmp) cudaFreeAsync(tmp, ctx->stream);
+        ctx_free(ctx, tmp);
         return cuda_fail(ctx, e, "evaluation kernel");
     }
     if (ptr_kind == QR_HOST) {
         QR_CU(ctx, cudaMemcpyAsync(y_out, dy, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
-        QR_CU(ctx, cudaFreeAsync(tmp, ctx->stream));
+        QR_CU(ctx, cudaStreamSynchronize(ctx->stream));
+        ctx_free(ctx, tmp);
     }
     QR_CU(ctx, cudaStreamSynchronize(ctx->stream));
     return QR_OK;
@@ -1250,12 +1281,12 @@ qr_status qr_test_points(const qr_ctx* ctx, int i, long long n, double* x_out)
     if (!ready(ctx) || !x_out || n < 0 || i < 0 || i > ctx->N) return QR_EINVAL;
     if (n == 0) return QR_OK;
     qr_ctx* c = const_cast<qr_ctx*>(ctx);
-    double* d = nullptr;
-    QR_CU(c, cudaMallocAsync(&d, sizeof(double) * (size_t)n * ctx->d, ctx->stream));
+    double* d = static_cast<double*>(ctx_malloc(c, sizeof(double) * (size_t)n * ctx->d));
+    if (!d) return fail(c, QR_ENOMEM, "qr_test_points: device allocation failed");
     cudaError_t e = launch_test_points(ctx->P, i, n, d, ctx->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(x_out, d, sizeof(double) * (size_t)n * ctx->d, cudaMemcpyDeviceToHost, ctx->stream);
-    cudaFreeAsync(d, ctx->stream);
+    ctx_free(c, d);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "test points");
     return QR_OK;
@@ -1390,6 +1421,21 @@ qr_status bfail(qr_batch* b, qr_status s, const std::string& m)
     return s;
 }
 
+// device tables of a batch: through its first context's allocator
+bool balloc(qr_batch* b, void** p, size_t bytes)
+{
+    *p = ctx_malloc(b->ctx[0], bytes);
+    // filled by synchronous copies: no earlier work on the stream may still use it
+    return *p != nullptr && cudaStreamSynchronize(b->ctx[0]->stream) == cudaSuccess;
+}
+void bfree(qr_batch* b, void* p)
+{
+    if (p && !b->ctx.empty()) {
+        cudaStreamSynchronize(b->ctx[0]->stream);
+        ctx_free(b->ctx[0], p);
+    }
+}
+
 // items of all instances, `tpi` tiles per item
 std::vector<BatchItem> batch_items(const qr_batch* b, int tpi)
 {
@@ -1424,9 +1470,9 @@ std::vector<BatchItem> batch_items(const qr_batch* b, int tpi)
 qr_status batch_set_items(qr_batch* b, int tpi)
 {
     std::vector<BatchItem> items = batch_items(b, tpi);
-    if (b->d_items) cudaFree(b->d_items);
+    bfree(b, b->d_items);
     b->d_items = nullptr;
-    if (cudaMalloc(&b->d_items, sizeof(BatchItem) * std::max<size_t>(1, items.size())) != cudaSuccess)
+    if (!balloc(b, reinterpret_cast<void**>(&b->d_items), sizeof(BatchItem) * std::max<size_t>(1, items.size())))
         return bfail(b, QR_ENOMEM, "batch items");
     if (cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return bfail(b, QR_ECUDA, "copy batch items");
@@ -1470,8 +1516,8 @@ bool shares_points(const qr_ctx* a, const qr_ctx* c)
 void free_groups(qr_batch* b)
 {
     for (BatchGroup& g : b->groups) {
-        if (g.d_inst) cudaFree(g.d_inst);
-        if (g.d_apack) cudaFree(g.d_apack);
+        bfree(b, g.d_inst);
+        bfree(b, g.d_apack);
     }
     b->groups.clear();
     b->grouped.assign(b->ctx.size(), 0);
@@ -1525,8 +1571,8 @@ qr_status batch_build_groups(qr_batch* b)
         }
         const int ntg = ((int)mem.size() + 31) / 32;
         const size_t abytes = (size_t)c->N * ntg * 2 * (size_t)group_block_elems(g.kind, g.d, g.n) * 2;
-        const bool ok = cudaMalloc(&g.d_inst, sizeof(GroupInst) * gi.size()) == cudaSuccess &&
-                        cudaMalloc(&g.d_apack, abytes) == cudaSuccess;
+        const bool ok = balloc(b, reinterpret_cast<void**>(&g.d_inst), sizeof(GroupInst) * gi.size()) &&
+                        balloc(b, &g.d_apack, abytes);
         b->groups.push_back(g);
         if (!ok) return bfail(b, QR_ENOMEM, "batch group allocation");
         if (cudaMemcpy(g.d_inst, gi.data(), sizeof(GroupInst) * gi.size(), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -1539,8 +1585,7 @@ qr_status batch_build_groups(qr_batch* b)
 void free_finish(qr_batch* b)
 {
     void* ptrs[] = {b->d_fin, b->d_fgroups, b->d_fitems, b->d_row_done, b->d_grp_done, b->d_resid};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    for (void* p : ptrs) bfree(b, p);
     b->d_fin = nullptr;
     b->d_fgroups = nullptr;
     b->d_fitems = nullptr;
@@ -1611,12 +1656,12 @@ qr_status batch_build_finish(qr_batch* b)
                 for (int ch = 0; ch < fi[q].P.n_chunks; ++ch) items.push_back(make_int4(q, i, ch, 0));
         }
     const bool ok =
-        cudaMalloc(&b->d_fin, sizeof(FinishInst) * n) == cudaSuccess &&
-        cudaMalloc(&b->d_fgroups, sizeof(FinishGroup) * std::max<size_t>(1, fg.size())) == cudaSuccess &&
-        cudaMalloc(&b->d_fitems, sizeof(int4) * std::max<size_t>(1, items.size())) == cudaSuccess &&
-        cudaMalloc(&b->d_row_done, sizeof(unsigned) * std::max(1, rows)) == cudaSuccess &&
-        cudaMalloc(&b->d_grp_done, sizeof(unsigned) * std::max(1, grows)) == cudaSuccess &&
-        cudaMalloc(&b->d_resid, sizeof(unsigned long long) * n) == cudaSuccess;
+        balloc(b, reinterpret_cast<void**>(&b->d_fin), sizeof(FinishInst) * n) &&
+        balloc(b, reinterpret_cast<void**>(&b->d_fgroups), sizeof(FinishGroup) * std::max<size_t>(1, fg.size())) &&
+        balloc(b, reinterpret_cast<void**>(&b->d_fitems), sizeof(int4) * std::max<size_t>(1, items.size())) &&
+        balloc(b, reinterpret_cast<void**>(&b->d_row_done), sizeof(unsigned) * std::max(1, rows)) &&
+        balloc(b, reinterpret_cast<void**>(&b->d_grp_done), sizeof(unsigned) * std::max(1, grows)) &&
+        balloc(b, reinterpret_cast<void**>(&b->d_resid), sizeof(unsigned long long) * n);
     if (!ok) {
         free_finish(b);
         return bfail(b, QR_ENOMEM, "batch finishing tables");
@@ -1702,8 +1747,8 @@ qr_status qr_batch_create(qr_batch** out, qr_ctx* const* ctxs, int n)
     }
     b->stream = ctxs[0]->stream;
     b->max_rowbytes = (maxrow + 15) & ~size_t(15);
-    if (cudaMalloc(&b->d_inst, sizeof(BatchInst) * n) != cudaSuccess ||
-        cudaMalloc(&b->d_next, sizeof(unsigned)) != cudaSuccess)
+    if (!balloc(b, reinterpret_cast<void**>(&b->d_inst), sizeof(BatchInst) * n) ||
+        !balloc(b, reinterpret_cast<void**>(&b->d_next), sizeof(unsigned)))
         return bfail(b, QR_ENOMEM, "batch allocation");
     if (cudaMemcpy(b->d_inst, inst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice) != cudaSuccess)
         return bfail(b, QR_ECUDA, "copy batch instances");
@@ -1865,9 +1910,9 @@ void qr_batch_destroy(qr_batch* b)
 {
     if (!b) return;
     if (b->graph) cudaGraphExecDestroy(b->graph);
-    if (b->d_inst) cudaFree(b->d_inst);
-    if (b->d_items) cudaFree(b->d_items);
-    if (b->d_next) cudaFree(b->d_next);
+    bfree(b, b->d_inst);
+    bfree(b, b->d_items);
+    bfree(b, b->d_next);
     free_finish(b);
     free_groups(b);
     for (auto& e : b->ev)

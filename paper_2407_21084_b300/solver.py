@@ -22,7 +22,7 @@ class Solver:
 
     def __init__(self, d, N, T, nu_kind, mu, gamma_kind, gamma_n, b, sigma, f_kind, f_par, g_kind, g_par, M,
                  seed, precision=L.QR_FP64, clamp_L=0.0, stream=None, lattice_n=0, instance=0, path_kernel=0,
-                 damping_q=0.0):
+                 damping_q=0.0, torch_memory=True):
         self._L = L.load()
         self.shard_world = 1
         self.d, self.N, self.T, self.M = int(d), int(N), float(T), int(M)
@@ -50,9 +50,12 @@ class Solver:
         else:
             stream_ptr = stream
         self.damping_q = float(damping_q)
+        # device buffers from PyTorch's caching allocator (the library's own
+        # stream-ordered allocation when torch_memory is False)
+        alloc, free = L.torch_allocator() if torch_memory and stream_ptr is not None else (None, None)
         opts = L.QrOpts(M, seed, precision, clamp_L, stream_ptr,
                         L.QR_U_LATTICE if lattice_n else L.QR_U_PHILOX, lattice_n, instance, path_kernel,
-                        self.damping_q)
+                        self.damping_q, alloc, free, None)
         self._ctx = C.c_void_p()
         st = self._L.qr_init(C.byref(self._ctx), d, N, T, C.byref(nu), C.byref(gam), _dp(b), _dp(sigma),
                              C.byref(f), C.byref(g), C.byref(opts))
