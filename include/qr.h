@@ -181,7 +181,9 @@ typedef struct {
 
 /* Creates a context: validates the problem, enumerates Gamma, allocates the
  * device state and sets alpha = 0 (ybar == 0 start).
- *   d in [1, 8]; N in [1, 256]; T > 0; b: d doubles (host); sigma: d*d doubles,
+ *   d in [1, 12] (index sets of Z^d, kinds 0-2, and the unfolded cosine route:
+ *   d <= 8; a cosine set with d > 8 runs on the direct route); N in [1, 256];
+ *   T > 0; b: d doubles (host); sigma: d*d doubles,
  *   row-major (host), X_{j+1} = X_j + b dt + sigma sqrt(dt) Z; every |k_l| <= 32767
  *   for d <= 4 and <= 127 above (QR_ENOTIMPL otherwise, or when the generic
  *   kernels' per-lane power tables and coefficient rows exceed shared memory);
@@ -332,7 +334,8 @@ qr_status qr_philox_words(const uint32_t* ctr_key, long long n, uint32_t* out);
 /* The device sampler of paths m0 .. m0+n-1 of row i: d start uniforms
  * (u_out, n*d, exact doubles), d start points F_nu^{-1}(u) (x_out, n*d)
  * and the d normals of Euler step j (z_out, n*d), computed in `precision`
- * (QR_FP32 results are widened to double). Host arrays; any may be NULL. */
+ * (QR_FP32 results are widened to double). Host arrays; any may be NULL.
+ * QR_EINVAL for d outside 1..8. */
 qr_status qr_sample(int d, const qr_nu* nu, unsigned long long seed, int instance, int i,
                     long long m0, long long n, int j, int precision, double* u_out,
                     double* x_out, double* z_out);

@@ -535,7 +535,7 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
         *out = c;
         return s;
     };
-    if (d < 1 || d > kDMax) return bail(QR_EINVAL, "d must be in [1, 8]");
+    if (d < 1 || d > kDMax) return bail(QR_EINVAL, "d must be in [1, 12]");
     if (N < 1 || N > kNMax) return bail(QR_EINVAL, "N must be in [1, 256]");
     if (!(T > 0.0) || !std::isfinite(T)) return bail(QR_EINVAL, "T must be positive");
     if (!nu || !gamma || !b || !sigma || !f || !g) return bail(QR_EINVAL, "null argument");
@@ -598,8 +598,10 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
         const size_t v2 = o.precision == QR_FP32 ? sizeof(float2) : sizeof(double2);
         const double need = (double)d * (km + 1) * 128 * v2 + 2.0 * (double)((nz + 1) / 2) * v2 + 256;
         const bool unfold_ok = km <= gentry_kmax(d) && need <= 227.0 * 1024;
-        c->cos_direct = o.path_kernel == 2 ||
+        c->cos_direct = o.path_kernel == 2 || d > kDMaxFourier ||
                         (o.path_kernel == 0 && (!unfold_ok || zkind == QR_G_HYP || tree_slots(zkind, d, gamma->n) == 0));
+        if (c->cos_direct && o.path_kernel == 1)
+            return bail(QR_ENOTIMPL, "the unfolded cosine route needs d <= 8 (path_kernel 0 or 2)");
         if (c->cos_direct) {
             c->k = std::move(kn);
             c->kmax = km;
@@ -639,13 +641,13 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
                 step_ok = step_ok && ke[l] == want;
             }
             if (!step_ok) return bail(QR_ENOTIMPL, "direct cosine kernels: Gamma is not downward closed");
-            uint32_t kz = 0, kw = 0;
+            uint32_t kz = 0, kw = 0, ky = 0;
             for (int l = 0; l + 1 < d; ++l) {
-                (l < 4 ? kz : kw) |= (uint32_t)ke[l] << (8 * (l & 3));
+                (l < 4 ? kz : (l < 8 ? kw : ky)) |= (uint32_t)ke[l] << (8 * (l & 3));
                 prev[l] = ke[l];
             }
             for (int a0 = 0; a0 < len; a0 += 4) {
-                cgroups.push_back(make_uint4((uint32_t)a0, 0u, kz, kw));
+                cgroups.push_back(make_uint4((uint32_t)a0, ky, kz, kw));
                 cflags.push_back((uint8_t)(a0 == 0 ? 0x80 | (e == 0 ? d - 1 : f) : d - 1));
             }
             e += len;
@@ -658,6 +660,7 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
         }
         c->cos_groups = (int)cgroups.size();
     } else {
+        if (d > kDMaxFourier) return bail(QR_ENOTIMPL, "index sets of Z^d need d <= 8");
         enumerate_gamma(zkind, d, gamma->n, c->k);
         if (cosine) {
             const int nz = (int)(c->k.size() / d);
@@ -709,7 +712,7 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
         first.assign(c->nGp, 0);
         for (int e = 0; e < c->nGp; ++e) {
             std::memset(tab[e].k8, 0, sizeof(tab[e].k8));
-            for (int l = 0; l < d && l < kDMax; ++l) tab[e].set(d, l, c->k[(size_t)(c->zero_idx + e) * d + l]);
+            for (int l = 0; l < d && l < kDMaxFourier; ++l) tab[e].set(d, l, c->k[(size_t)(c->zero_idx + e) * d + l]);
             if (e > 0) {
                 int f0 = 0;
                 while (f0 < d && tab[e].get(d, f0) == tab[e - 1].get(d, f0)) ++f0;
@@ -1315,7 +1318,7 @@ qr_status qr_philox_words(const uint32_t* ctr_key, long long n, uint32_t* out)
 qr_status qr_sample(int d, const qr_nu* nu, unsigned long long seed, int instance, int i, long long m0, long long n,
                     int j, int precision, double* u_out, double* x_out, double* z_out)
 {
-    if (d < 1 || d > kDMax || !nu || n < 0 || m0 < 0 || i < 0 || i >= 65536 || instance < 0 || instance >= 4096 ||
+    if (d < 1 || d > kDMaxFourier || !nu || n < 0 || m0 < 0 || i < 0 || i >= 65536 || instance < 0 || instance >= 4096 ||
         (precision != QR_FP32 && precision != QR_FP64))
         return QR_EINVAL;
     if (n == 0) return QR_OK;
@@ -1350,7 +1353,7 @@ qr_status qr_sample(int d, const qr_nu* nu, unsigned long long seed, int instanc
 qr_status qr_sample_normals_tree(int d, unsigned long long seed, int instance, int i, long long m0, long long n,
                                  int j, double* z_out)
 {
-    if (d < 1 || d > kDMax || !z_out || n < 0 || m0 < 0 || i < 0 || i >= 65536 || instance < 0 || instance >= 4096)
+    if (d < 1 || d > kDMaxFourier || !z_out || n < 0 || m0 < 0 || i < 0 || i >= 65536 || instance < 0 || instance >= 4096)
         return QR_EINVAL;
     if (n == 0) return QR_OK;
     QrParams P{};

@@ -123,13 +123,13 @@ struct CosWalk {
 
     // prefix k_1..k_{d-1} from scratch (bytes of kz, kw) and the last
     // coordinate at a0: the state before the group that starts at a0
-    __device__ __forceinline__ void seek(uint32_t kz, uint32_t kw, int a0, R b0)
+    __device__ __forceinline__ void seek(uint32_t kz, uint32_t kw, uint32_t ky, int a0, R b0)
     {
         const R r2 = (R)1.4142135623730951;
         if constexpr (D > 1) {
 #pragma unroll
             for (int l = 0; l < D - 1; ++l) {
-                const int k = (int)(((l < 4 ? kz : kw) >> (8 * (l & 3))) & 0xffu);
+                const int k = (int)(((l < 4 ? kz : (l < 8 ? kw : ky)) >> (8 * (l & 3))) & 0xffu);
                 V2<R> v = mk2<R>(r2, (R)0);
                 for (int t = 0; t < k; ++t) v = cmul<R>(v, z[l]);
                 w[l] = v;
@@ -176,7 +176,7 @@ __device__ __forceinline__ uint32_t word_of(const uint4& v, int h)
 }
 
 // sum_k c_k phi_k at the walk's point; c: packed real row (groups of 4),
-// flags: one byte per group (bit 7: a run starts, bits 0-2: its first
+// flags: one byte per group (bit 7: a run starts, bits 0-3: its first
 // changed prefix coordinate, d-1 for none), ng a multiple of 16
 template <typename R, int D>
 __device__ __forceinline__ R cos_series(const R* __restrict__ c, const uint4* __restrict__ flags, int ng,
@@ -201,7 +201,7 @@ __device__ __forceinline__ R cos_series(const R* __restrict__ c, const uint4* __
                     acc = fma(W.p, s0 + s1, acc);
                     s0 = (R)0;
                     s1 = (R)0;
-                    if (D > 1 && (int)(fb & 7u) < D - 1) W.new_run((int)(fb & 7u), (R)1);
+                    if (D > 1 && (int)(fb & 15u) < D - 1) W.new_run((int)(fb & 15u), (R)1);
                 }
                 R v0, v1, v2, v3;
                 W.values(start, v0, v1, v2, v3);
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kCosBS, PPL == 2 ? 3 : (sizeof(R) == 4 ? 4 : 2
             V2<R> ph[D];
             start_phases_dev<R, D>(P, i, active ? m : 0, ph);  // e^{i pi U^m} (half angle)
             Wk[u].init(ph, Sv[u]);
-            Wk[u].seek(q0.z, q0.w, a00, Sv[u]);
+            Wk[u].seek(q0.z, q0.w, q0.y, a00, Sv[u]);
         }
         for (int g0 = gs; g0 < ge; g0 += 8) {
             const uint2 fl = __ldg(reinterpret_cast<const uint2*>(flags) + g0 / 8);
@@ -430,8 +430,8 @@ __global__ void __launch_bounds__(kCosBS, PPL == 2 ? 3 : (sizeof(R) == 4 ? 4 : 2
 #pragma unroll
                 for (int u = 0; u < PPL; ++u) {
                     // (the pass's first group: seek placed the walk on its run already)
-                    if (D > 1 && start && (int)(fb & 7u) < D - 1 && g0 + gg != gs)
-                        Wk[u].new_run((int)(fb & 7u), Sv[u]);
+                    if (D > 1 && start && (int)(fb & 15u) < D - 1 && g0 + gg != gs)
+                        Wk[u].new_run((int)(fb & 15u), Sv[u]);
                     R v0, v1, v2, v3;
                     Wk[u].values(start, v0, v1, v2, v3);
                     if (u == 0) {
@@ -588,7 +588,7 @@ template <typename R, int D>
 cudaError_t project_cos_t(const QrParams& P, const CosGroup* G, const uint4* flags, int ngroups, const void* S,
                           double* partial, long long row_stride, int i_lo, int i_hi, cudaStream_t st)
 {
-    if (sizeof(R) == 4 && P.chunk % (2 * kCosBS) == 0)
+    if (sizeof(R) == 4 && D <= 8 && P.chunk % (2 * kCosBS) == 0)
         return project_cos_ppl<R, D, 2>(P, G, flags, ngroups, S, partial, row_stride, i_lo, i_hi, st);
     return project_cos_ppl<R, D, 1>(P, G, flags, ngroups, S, partial, row_stride, i_lo, i_hi, st);
 }
@@ -616,6 +616,10 @@ cudaError_t eval_cos_t(const QrParams& P, const uint4* flags, int ng, const void
     case 6: return FN<R, 6>(__VA_ARGS__);  \
     case 7: return FN<R, 7>(__VA_ARGS__);  \
     case 8: return FN<R, 8>(__VA_ARGS__);  \
+    case 9: return FN<R, 9>(__VA_ARGS__);  \
+    case 10: return FN<R, 10>(__VA_ARGS__); \
+    case 11: return FN<R, 11>(__VA_ARGS__); \
+    case 12: return FN<R, 12>(__VA_ARGS__); \
     default: return cudaErrorInvalidValue; \
     }
 

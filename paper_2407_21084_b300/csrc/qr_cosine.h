@@ -16,12 +16,12 @@ namespace qr {
 // coordinate f, which is one larger, and the prefix coordinates after f are
 // 0 (lexicographic order of a downward-closed set; checked by qr_init): the
 // kernels step every factor by one complex product. Per group they read one
-// flag byte: bit 7 = a run starts here, bits 0-2 = f (d-1 for the first run
+// flag byte: bit 7 = a run starts here, bits 0-3 = f (d-1 for the first run
 // and the padding, whose prefix is all zeros or unchanged).
 //
 // CosGroup (16 bytes, for starting a walk in the middle of Gamma):
 //   x: a0 = k_d of the group's first position (bits 0-15)
-//   z, w: k_1..k_4 and k_5..k_7 of the run's prefix, one byte each
+//   z, w, y: k_1..k_4, k_5..k_8 and k_9..k_11 of the run's prefix, one byte each
 using CosGroup = uint4;
 
 constexpr int kCosPrefixMax = 255;  // prefix coordinates are stored in one byte

@@ -8,7 +8,8 @@
 
 namespace qr {
 
-constexpr int kDMax = 8;    // dimensions
+constexpr int kDMax = 12;       // dimensions (the direct cosine kernels)
+constexpr int kDMaxFourier = 8; // dimensions of the Z^d sets (table entries hold 8 coordinates)
 constexpr int kNMax = 256;  // time steps
 
 enum { QR_TAG_START = 0, QR_TAG_INCR = 1, QR_TAG_TEST = 2 };

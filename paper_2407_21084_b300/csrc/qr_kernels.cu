@@ -772,6 +772,10 @@ cudaError_t launch_test_points(const QrParams& P, int i, long long n, double* x,
     case 6: return test_points_t<6>(P, i, n, x, st);
     case 7: return test_points_t<7>(P, i, n, x, st);
     case 8: return test_points_t<8>(P, i, n, x, st);
+    case 9: return test_points_t<9>(P, i, n, x, st);
+    case 10: return test_points_t<10>(P, i, n, x, st);
+    case 11: return test_points_t<11>(P, i, n, x, st);
+    case 12: return test_points_t<12>(P, i, n, x, st);
     default: return cudaErrorInvalidValue;
     }
 }

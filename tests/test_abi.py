@@ -62,7 +62,8 @@ def _init(lib, d=2, N=4, T=1.0, gamma=(1, 2), M=64, prec=0, fkind=0, gkind=0, nu
 
 
 @pytest.mark.parametrize("kw,frag", [
-    (dict(d=0), "d must"), (dict(d=9), "d must"), (dict(N=0), "N must"), (dict(N=257), "N must"),
+    (dict(d=0), "d must"), (dict(d=13), "d must"), (dict(d=9), "Z^d need d <= 8"),
+    (dict(d=9, gamma=(5, 1), kern=1), "unfolded cosine route needs d <= 8"), (dict(N=0), "N must"), (dict(N=257), "N must"),
     (dict(T=-1.0), "T must"), (dict(M=0), "M must"), (dict(prec=7), "precision"),
     (dict(gamma=(6, 2)), "index set"), (dict(gamma=(5, 0)), "index set"), (dict(d=5, gamma=(2, 128)), "|k_l| <= 127"),
     (dict(d=1, gamma=(0, 40000)), "|k_l| <= 32767"),

@@ -3,7 +3,8 @@ C_a(u) = sqrt(2) cos(a pi u), runs of Gamma over the last coordinate, groups
 of 4 packed positions) against the FP64 oracle on the sets the unfolded
 route cannot take (the paper's d = 5 and d = 7 hyperbolic-cross sets of
 Sec. 5), at the edges of the group layout (d = 1 with a single entry, d = 8,
-prefix bytes of both words), through qr_eval, against the unfolded route,
+prefix bytes of both words), above d = 8 (the paper's d = 9 and d = 11
+hyperbolic-cross sets with their damping exponents, d = 12), through qr_eval, against the unfolded route,
 and at the full size of the paper's d = 5, Delta = 0.2, DEG = 16 row
 (M = 2 10^6) on sampled responses."""
 import numpy as np
@@ -43,6 +44,12 @@ def _oracle_problem(ora, p: W.Sec5Problem, M=None):
     (6, W.G_HYP_N, 9, 2, 333, 0.0, (0, 1)),      # prefix bytes in both words
     (8, W.G_TOTAL_N, 3, 3, 400, 5.1, (0, 1)),    # d = 8: seven prefix coordinates
     (7, W.G_HYP_N, 36, 2, 300, 5.1, (0, 1)),     # the paper's d = 7 set, 94460 entries: rows from global memory
+    (9, W.G_HYP_N, 2, 3, 300, 17.6, (0, 1)),     # d = 9: a prefix coordinate in the third word
+    (9, W.G_HYP_N, 5, 2, 120, 17.6, (0,)),       # the paper's d = 9 set Gamma_H(5), 14336 entries, its q
+    (10, W.G_TOTAL_N, 3, 2, 257, 0.0, (0, 1)),
+    (11, W.G_HYP_N, 2, 2, 150, 21.6, (0,)),      # the paper's d = 11 set Gamma_H(2), 13312 entries, its q
+    (11, W.G_HYP_N, 1, 3, 200, 2.1, (0, 1)),     # {0,1}^11
+    (12, W.G_TOTAL_N, 2, 3, 333, 5.1, (0, 1)),   # d = 12, the largest: eleven prefix coordinates
 ])
 def test_direct_picard_matches_oracle(mods, ora, d, kind, n, N, M, q, precs):
     solver, L = mods
@@ -120,6 +127,23 @@ def test_direct_eval_matches_oracle_series(mods, ora, d, kind, n):
                 got = s.eval(i, x)
                 want = ora.series(op, a[i].astype(complex), x)
                 assert np.abs(got - want).max() < tol * B, (prec, i)
+
+
+@pytest.mark.parametrize("d", [9, 12])
+def test_routes_above_d8(mods, d):
+    """Above d = 8 the direct route is the only one: the automatic choice
+    takes it, the unfolded route and the Z^d (Fourier) sets are refused."""
+    solver, L = mods
+    p = W.Sec5Problem(d=d, N=2, gamma_kind=W.G_HYP_N, gamma_n=1, M=128, seed=4)
+    with solver.Solver.from_sec5(p, precision=1) as s:
+        s.picard_step(1)
+        assert s.nG == 2 ** d
+    with pytest.raises(L.QrError) as e:
+        solver.Solver.from_sec5(p, precision=1, path_kernel=1)
+    assert e.value.status == L.QR_ENOTIMPL
+    with pytest.raises(L.QrError):
+        solver.Solver(d, 2, 1.0, L.QR_NU_STUDENT2, 2.0, L.QR_G_L1, 1, np.zeros(d), np.eye(d), L.QR_F_ZERO, [0.0],
+                      L.QR_GT_COS, np.ones(d), 64, 1, precision=1)
 
 
 def test_direct_rejects_fourier_sets(mods):
