@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <complex>
 #include <functional>
 #include <new>
 #include <string>
@@ -136,10 +137,19 @@ void enumerate_gamma(int kind, int d, int n, std::vector<int>& out, bool nonneg 
     rec(0, 0, 1);
 }
 
-// Tree layout of the half set (mirrors the traversal of qr_fast.cu): the
+// Tree layout of the half set (mirrors the traversal of qr_tree.cuh): the
 // root slot, then for each dimension the subtree of +e_l; a node's slot is
 // followed by its extension child and its children in the later dimensions,
-// whose + and - subtrees follow each other; +-1 leaf pairs are pre-combined.
+// whose + and - subtrees follow each other; +-1 leaf pairs and the mirrored
+// chains of the last dimension are pre-combined pairs; with QR_TREE_PAIR_D2
+// the mirrored chains of the second-to-last dimension are, per m, a sum
+// subtree A_m and a difference subtree B_m of pre-combined coefficients.
+//
+// A slot is a real-linear form in the coefficient row; it is built from
+// "virtual coefficients" v = sum_t f_t alpha_{e_t} (f_t complex), of which
+// every traversal position sees one: alpha_k itself, or alpha_k +
+// alpha_k' (A) and i alpha_k - i alpha_k' (B), k' = k mirrored in
+// dimension d-2.
 bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vector<TreeMap>& out)
 {
     const int nG = (int)(K.size() / d);
@@ -152,9 +162,44 @@ bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vect
     idx.reserve(nG);
     for (int e = 0; e < nG; ++e) idx.emplace_back(key(std::vector<int>(K.begin() + (size_t)e * d, K.begin() + (size_t)(e + 1) * d)), e);
     std::sort(idx.begin(), idx.end());
+    bool ok = true;
     auto find = [&](const std::vector<int>& k) {
         auto it = std::lower_bound(idx.begin(), idx.end(), std::make_pair(key(k), -1));
-        return (it != idx.end() && it->first == key(k)) ? it->second : -1;
+        if (it != idx.end() && it->first == key(k)) return it->second;
+        ok = false;
+        return 0;
+    };
+    using VC = std::vector<std::pair<int, std::complex<double>>>;  // sum f alpha_e
+    using CoefFn = std::function<VC(const std::vector<int>&)>;
+    const CoefFn plain = [&](const std::vector<int>& k) { return VC{{find(k), 1.0}}; };
+    // term `coef * a[ix]` into row h of a slot (merged with a term of the same index)
+    auto put = [&](TreeMap& m, int h, int ix, double coef) {
+        if (coef == 0.0) return;
+        for (int t = 0; t < 4; ++t) {
+            if (m.c[h][t] != 0.0 && m.i[h][t] == ix) {
+                m.c[h][t] += coef;
+                return;
+            }
+            if (m.c[h][t] == 0.0) {
+                m.i[h][t] = ix;
+                m.c[h][t] = coef;
+                return;
+            }
+        }
+        ok = false;  // more than four terms
+    };
+    // s Re v and s Im v: Re(f a) = f.re a.re - f.im a.im, Im(f a) = f.re a.im + f.im a.re
+    auto re_into = [&](TreeMap& m, int h, const VC& v, double sc) {
+        for (const auto& t : v) {
+            put(m, h, 2 * t.first, sc * t.second.real());
+            put(m, h, 2 * t.first + 1, -sc * t.second.imag());
+        }
+    };
+    auto im_into = [&](TreeMap& m, int h, const VC& v, double sc) {
+        for (const auto& t : v) {
+            put(m, h, 2 * t.first + 1, sc * t.second.real());
+            put(m, h, 2 * t.first, sc * t.second.imag());
+        }
     };
     const bool l1 = kind == QR_G_L1;
     auto ext_ok = [&](int S) { return l1 ? S >= 1 : S < n; };
@@ -162,28 +207,27 @@ bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vect
     auto new_ok = [&](int S) { return l1 ? S >= 1 : true; };
     auto new_S = [&](int S) { return l1 ? S - 1 : 1; };
     auto leaf = [&](int L, int S) { return l1 ? S == 0 : (S == n && L == d - 1); };
-    bool ok = true;
     int emitted = 0;
-    auto single = [&](const std::vector<int>& k) {
-        const int e = find(k);
-        if (e < 0) ok = false;
+    // a slot holding 2v (the factor 2 of the half-set sum)
+    auto single = [&](const VC& v) {
         TreeMap m{};
-        m.i[0][0] = 2 * std::max(e, 0);
-        m.c[0][0] = 2.0;
-        m.i[1][0] = 2 * std::max(e, 0) + 1;
-        m.c[1][0] = 2.0;
+        re_into(m, 0, v, 2.0);
+        im_into(m, 1, v, 2.0);
         out.push_back(m);
         ++emitted;
     };
-    auto pair = [&](const std::vector<int>& kp, const std::vector<int>& km) {
-        const int ep = std::max(find(kp), 0), em = std::max(find(km), 0);
-        if (find(kp) < 0 || find(km) < 0) ok = false;
-        // slots (A, C) and (B, E): T += (A, C) (z.x, z.y) + (B, E) (z.y, z.x)
+    // slots (A, C) and (B, E) of v+ w + v- conj(w): T += (A, C) (w.x, w.y) + (B, E) (w.y, w.x),
+    // A = a+ + a-, C = a+ - a-, B = b- - b+, E = b+ + b- (a = 2 Re v, b = 2 Im v)
+    auto pair = [&](const VC& vp, const VC& vm) {
         TreeMap a{}, b{};
-        a.i[0][0] = 2 * ep; a.c[0][0] = 2.0; a.i[0][1] = 2 * em; a.c[0][1] = 2.0;           // A = a+ + a-
-        a.i[1][0] = 2 * ep; a.c[1][0] = 2.0; a.i[1][1] = 2 * em; a.c[1][1] = -2.0;          // C = a+ - a-
-        b.i[0][0] = 2 * em + 1; b.c[0][0] = 2.0; b.i[0][1] = 2 * ep + 1; b.c[0][1] = -2.0;  // B = b- - b+
-        b.i[1][0] = 2 * ep + 1; b.c[1][0] = 2.0; b.i[1][1] = 2 * em + 1; b.c[1][1] = 2.0;   // E = b+ + b-
+        re_into(a, 0, vp, 2.0);
+        re_into(a, 0, vm, 2.0);
+        re_into(a, 1, vp, 2.0);
+        re_into(a, 1, vm, -2.0);
+        im_into(b, 0, vm, 2.0);
+        im_into(b, 0, vp, -2.0);
+        im_into(b, 1, vp, 2.0);
+        im_into(b, 1, vm, 2.0);
         out.push_back(a);
         out.push_back(b);
         emitted += 2;
@@ -198,46 +242,80 @@ bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vect
         }
         return len;
     };
-    std::function<void(int, int, std::vector<int>)> node = [&](int L, int S, std::vector<int> k) {
-        single(k);
+    auto shifted = [](std::vector<int> k, int l, int by) {
+        k[l] += by;
+        return k;
+    };
+    // children in the last dimension of a node k in state S
+    auto last_children = [&](const std::vector<int>& k, int S, const CoefFn& cf) {
+        const int l2 = d - 1;
+        if (leaf(l2, new_S(S))) {
+            pair(cf(shifted(k, l2, 1)), cf(shifted(k, l2, -1)));
+        } else {
+            // the mirrored chains k +- m e_{d-1} as pairs, m = 1..len
+            const int len = chain_len(new_S(S));
+            for (int m = 1; m <= len; ++m) pair(cf(shifted(k, l2, m)), cf(shifted(k, l2, -m)));
+        }
+    };
+    // the mirrored chains k +- m e_{d-2} of a node k (k_{d-2} = 0) whose
+    // children there start in state S2: per m the slots of A_m then B_m
+    auto pair2_chain = [&](const std::vector<int>& k, int S2, const CoefFn& cf) {
+        const int l2 = d - 2;
+        for (int m = 1, S = S2;; ++m) {
+            const std::vector<int> kp = shifted(k, l2, m);
+            const CoefFn ca = [&, m](const std::vector<int>& q) {
+                VC v = cf(q);
+                const VC w = cf(shifted(q, l2, -2 * m));
+                v.insert(v.end(), w.begin(), w.end());
+                return v;
+            };
+            const CoefFn cb = [&, m](const std::vector<int>& q) {
+                VC v = cf(q), w = cf(shifted(q, l2, -2 * m));
+                for (auto& t : v) t.second *= std::complex<double>(0.0, 1.0);
+                for (auto& t : w) v.emplace_back(t.first, t.second * std::complex<double>(0.0, -1.0));
+                return v;
+            };
+            single(ca(kp));
+            single(cb(kp));
+            if (leaf(l2, S)) break;
+            if (new_ok(S)) {
+                last_children(kp, S, ca);
+                last_children(kp, S, cb);
+            }
+            if (!ext_ok(S)) break;
+            S = ext_S(S);
+        }
+    };
+    std::function<void(int, int, const std::vector<int>&)> node = [&](int L, int S, const std::vector<int>& k) {
+        single(plain(k));
         if (ext_ok(S)) {
-            std::vector<int> k2 = k;
-            k2[L] += k[L] > 0 ? 1 : -1;
-            if (leaf(L, ext_S(S))) single(k2);
+            const std::vector<int> k2 = shifted(k, L, k[L] > 0 ? 1 : -1);
+            if (leaf(L, ext_S(S))) single(plain(k2));
             else node(L, ext_S(S), k2);
         }
         if (new_ok(S))
             for (int l2 = L + 1; l2 < d; ++l2) {
-                std::vector<int> kp = k, km = k;
-                kp[l2] += 1;
-                km[l2] -= 1;
                 if (leaf(l2, new_S(S))) {
-                    pair(kp, km);
+                    pair(plain(shifted(k, l2, 1)), plain(shifted(k, l2, -1)));
                 } else if (l2 == d - 1) {
-                    // the mirrored chains k +- m e_{d-1} as pairs, m = 1..len
-                    const int len = chain_len(new_S(S));
-                    for (int m = 1; m <= len; ++m) {
-                        std::vector<int> cp = k, cm = k;
-                        cp[l2] += m;
-                        cm[l2] -= m;
-                        pair(cp, cm);
-                    }
+                    last_children(k, S, plain);
+                } else if (QR_TREE_PAIR_D2 && l2 == d - 2) {
+                    pair2_chain(k, new_S(S), plain);
                 } else {
-                    node(l2, new_S(S), kp);
-                    node(l2, new_S(S), km);
+                    node(l2, new_S(S), shifted(k, l2, 1));
+                    node(l2, new_S(S), shifted(k, l2, -1));
                 }
             }
     };
     std::vector<int> zero(d, 0);
     TreeMap r{};
-    r.i[0][0] = 2 * find(zero);
-    r.c[0][0] = 1.0;
+    re_into(r, 0, plain(zero), 1.0);
+    im_into(r, 1, plain(zero), 1.0);
     out.push_back(r);
     const int S0 = l1 ? n - 1 : 1;
     for (int l = 0; l < d; ++l) {
-        std::vector<int> k = zero;
-        k[l] = 1;
-        if (leaf(l, S0)) single(k);
+        const std::vector<int> k = shifted(zero, l, 1);
+        if (leaf(l, S0)) single(plain(k));
         else node(l, S0, k);
     }
     return ok && emitted == (nG - 1) / 2;

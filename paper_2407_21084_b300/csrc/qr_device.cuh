@@ -25,10 +25,17 @@ template <typename R> __device__ __forceinline__ V2<R> mk2(R a, R b);
 template <> __device__ __forceinline__ float2 mk2<float>(float a, float b) { return make_float2(a, b); }
 template <> __device__ __forceinline__ double2 mk2<double>(double a, double b) { return make_double2(a, b); }
 
+// a product the compiler never fuses into an FMA
+template <typename R> __device__ __forceinline__ R mul_rn(R a, R b);
+template <> __device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+
+// complex product with its roundings fixed in the source (one product
+// rounded, one fused), so that every kernel inlining it rounds alike
 template <typename R>
 __device__ __forceinline__ V2<R> cmul(V2<R> a, V2<R> b)
 {
-    return mk2<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return mk2<R>(fma(a.x, b.x, -mul_rn<R>(a.y, b.y)), fma(a.x, b.y, mul_rn<R>(a.y, b.x)));
 }
 
 // ------------------------------------------------------------------ Philox

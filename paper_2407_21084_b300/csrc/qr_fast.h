@@ -5,13 +5,22 @@
 
 namespace qr {
 
-// One slot of the tree layout: slot.x = c[0][0] a[i[0][0]] + c[0][1] a[i[0][1]],
-// slot.y likewise with row 1, where a is a master coefficient row seen as
-// 2|Gamma| doubles (re, im interleaved).
+// One slot of the tree layout: slot.x = sum_t c[0][t] a[i[0][t]] (t < 4,
+// terms with c = 0 skipped), slot.y likewise with row 1, where a is a master
+// coefficient row seen as 2|Gamma| doubles (re, im interleaved).
 struct TreeMap {
-    int i[2][2];
-    double c[2][2];
+    int i[2][4];
+    double c[2][4];
 };
+
+// The mirrored chains k +- m e_{d-2} of the second-to-last dimension are
+// evaluated in pair form (one sum and one difference subtree per m against
+// the powers of that dimension's phase) instead of two Horner chains; the
+// device traversal (qr_tree.cuh) and the host layout (build_tree_map)
+// both follow this switch.
+#ifndef QR_TREE_PAIR_D2
+#define QR_TREE_PAIR_D2 1
+#endif
 
 // number of slots of the compiled tree for (kind, d, n); 0 if not compiled
 int tree_slots(int kind, int d, int n);

@@ -72,8 +72,9 @@ __device__ __forceinline__ V2<R> tree_slot(const double* a, const TreeMap& mp)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         double t = 0.0;
-        if (mp.c[h][0] != 0) t += mp.c[h][0] * a[mp.i[h][0]];
-        if (mp.c[h][1] != 0) t += mp.c[h][1] * a[mp.i[h][1]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (mp.c[h][u] != 0) t += mp.c[h][u] * a[mp.i[h][u]];
         v[h] = t;
     }
     return mk2<R>((R)v[0], (R)v[1]);

@@ -62,11 +62,14 @@ struct TreeShape {
 };
 
 // the phases of one path point as the tree evaluation sees them: z[p][l] =
-// e^{2 pi i F(x_l)} and the powers zl[p][m] = z[p][D-1]^{m+1}
+// e^{2 pi i F(x_l)}, the powers zl[p][m] = z[p][D-1]^{m+1} and, for the pair
+// form of the second-to-last dimension, zk[p][m] = z[p][D-2]^{m+1}
 template <typename R, int P, int D, int NPW>
 struct TreePh {
+    static constexpr int NK = (QR_TREE_PAIR_D2 && D >= 3) ? NPW : 1;
     V2<R> z[P][D];
     V2<R> zl[P][NPW];
+    V2<R> zk[P][NK];
 };
 
 template <typename R>
@@ -346,6 +349,60 @@ __device__ __forceinline__ void pair_acc(V2<R>& T, V2<R> ac, V2<R> be, V2<R> w)
     T.y = fma(be.y, w.x, T.y);
 }
 
+// T += Re(w) A + Im(w) B, 4 FMA (two packed in the FP32 form)
+template <typename R>
+__device__ __forceinline__ void rs_acc(V2<R>& T, V2<R> A, V2<R> B, V2<R> w)
+{
+#if QR_TREE_PAIR2
+    if constexpr (sizeof(R) == 4) {
+        T = __ffma2_rn(A, make_float2(w.x, w.x), T);
+        T = __ffma2_rn(B, make_float2(w.y, w.y), T);
+        return;
+    }
+#endif
+    T.x = fma(A.x, w.x, T.x);
+    T.y = fma(A.y, w.x, T.y);
+    T.x = fma(B.x, w.y, T.x);
+    T.y = fma(B.y, w.y, T.y);
+}
+
+template <typename R, int D, int NN, int KIND, int P, int L2, int S>
+struct NewDims;
+
+// The + and - chains k +- m e_{D-2} of the second-to-last dimension below a
+// node (position MM = m - 1 of the chain, node state S2). With U+-_m the
+// subtree values at k +- m e_{D-2} without their extensions (both in the
+// last dimension's phase) the chains contribute
+//   sum_m (w^m U+_m + conj(w)^m U-_m) = sum_m (Re(w^m) A_m + Im(w^m) B_m),
+// A_m = U+_m + U-_m, B_m = i (U+_m - U-_m), both evaluated as subtrees of
+// the same shape from pre-combined coefficients; each mirrored pair of
+// nodes then costs 4 FMA against the powers w^m instead of two Horner edges.
+template <typename R, int D, int NN, int KIND, int P, int S2, int MM>
+struct Pair2Chain {
+    using Sh = TreeShape<D, NN, KIND>;
+    using Ph = TreePh<R, P, D, Sh::npow()>;
+    static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, int& off, V2<R> (&T)[P], const Ph& z)
+    {
+        static_assert(MM < Ph::NK, "power table too short");
+        V2<R> A[P], B[P];
+        const V2<R> ca = c[off], cb = c[off + 1];
+        off += 2;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            A[p] = ca;
+            B[p] = cb;
+        }
+        if constexpr (!Sh::leaf(D - 2, S2) && Sh::new_ok(S2)) {
+            NewDims<R, D, NN, KIND, P, D - 1, S2>::run(c, off, A, z);
+            NewDims<R, D, NN, KIND, P, D - 1, S2>::run(c, off, B, z);
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) rs_acc<R>(T[p], A[p], B[p], z.zk[p][MM]);
+        if constexpr (!Sh::leaf(D - 2, S2) && Sh::ext_ok(S2))
+            Pair2Chain<R, D, NN, KIND, P, Sh::ext_S(S2), MM + 1>::run(c, off, T, z);
+    }
+};
+
 // children in the new dimensions L2 .. D-1 of a node in state S
 template <typename R, int D, int NN, int KIND, int P, int L2, int S>
 struct NewDims {
@@ -375,6 +432,8 @@ struct NewDims {
                     for (int p = 0; p < P; ++p) pair_acc<R>(T[p], ac, be, z.zl[p][mm]);
                 }
                 off += 2 * len;
+            } else if constexpr (QR_TREE_PAIR_D2 && L2 == D - 2) {
+                Pair2Chain<R, D, NN, KIND, P, S2, 0>::run(c, off, T, z);
             } else {
                 constexpr int sz = Sh::size(L2, S2);
                 const V2<R>* cs = c + off;
@@ -485,6 +544,11 @@ __device__ __forceinline__ void tree_series(const V2<R>* __restrict__ c, const V
         ph.zl[p][0] = z[p][D - 1];
 #pragma unroll
         for (int m = 1; m < Sh::npow(); ++m) ph.zl[p][m] = cmul<R>(ph.zl[p][m - 1], z[p][D - 1]);
+        if constexpr (QR_TREE_PAIR_D2 && D >= 3) {
+            ph.zk[p][0] = z[p][D - 2];
+#pragma unroll
+            for (int m = 1; m < decltype(ph)::NK; ++m) ph.zk[p][m] = cmul<R>(ph.zk[p][m - 1], z[p][D - 2]);
+        }
     }
     V2<R> T[P];
     const V2<R> c0 = c[0];
