@@ -308,8 +308,11 @@ void qr_batch_destroy(qr_batch* b);
  * kernels (tiled GEMM with fused bias/GELU, GELU backward, Adam).
  * Buffers X (B x n_in), T and Y (B x n_out) are row-major FP32 device
  * arrays of the caller; B <= max_batch. Parameters are one flat FP32 array:
- * for each layer W (n_in x n_out, row-major) then b. Every call returns a
- * qr_status; qr_mlp_last_error gives text. */
+ * for each layer W (n_in x n_out, row-major) then b. All device work runs on
+ * `stream` (NULL: the legacy default stream), so X and T must be ready in
+ * that stream's order; qr_mlp_train_step returns without waiting (unless
+ * loss_out is given), the other calls wait for the stream before returning.
+ * Every call returns a qr_status; qr_mlp_last_error gives text. */
 typedef struct qr_mlp qr_mlp;
 qr_status qr_mlp_create(qr_mlp** out, int n_in, int width, int depth, int n_out, int max_batch,
                         unsigned long long seed, void* stream);

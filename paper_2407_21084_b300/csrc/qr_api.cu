@@ -141,15 +141,15 @@ void enumerate_gamma(int kind, int d, int n, std::vector<int>& out, bool nonneg 
 // root slot, then for each dimension the subtree of +e_l; a node's slot is
 // followed by its extension child and its children in the later dimensions,
 // whose + and - subtrees follow each other; +-1 leaf pairs and the mirrored
-// chains of the last dimension are pre-combined pairs; with QR_TREE_PAIR_D2
-// the mirrored chains of the second-to-last dimension are, per m, a sum
-// subtree A_m and a difference subtree B_m of pre-combined coefficients.
+// chains of the last dimension are pre-combined pairs; the mirrored chains of
+// the QR_TREE_PAIR_LEVELS dimensions before it are, per m, a sum subtree A_m
+// and a difference subtree B_m of pre-combined coefficients.
 //
 // A slot is a real-linear form in the coefficient row; it is built from
 // "virtual coefficients" v = sum_t f_t alpha_{e_t} (f_t complex), of which
-// every traversal position sees one: alpha_k itself, or alpha_k +
-// alpha_k' (A) and i alpha_k - i alpha_k' (B), k' = k mirrored in
-// dimension d-2.
+// every traversal position sees one: alpha_k itself or, inside a pair
+// chain of dimension l, v(k) + v(k') (A) and i v(k) - i v(k') (B) of the
+// enclosing virtual coefficient v, k' = k mirrored in dimension l.
 bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vector<TreeMap>& out)
 {
     const int nG = (int)(K.size() / d);
@@ -175,7 +175,7 @@ bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vect
     // term `coef * a[ix]` into row h of a slot (merged with a term of the same index)
     auto put = [&](TreeMap& m, int h, int ix, double coef) {
         if (coef == 0.0) return;
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < kTreeTerms; ++t) {
             if (m.c[h][t] != 0.0 && m.i[h][t] == ix) {
                 m.c[h][t] += coef;
                 return;
@@ -186,7 +186,7 @@ bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vect
                 return;
             }
         }
-        ok = false;  // more than four terms
+        ok = false;  // more terms than a slot holds
     };
     // s Re v and s Im v: Re(f a) = f.re a.re - f.im a.im, Im(f a) = f.re a.im + f.im a.re
     auto re_into = [&](TreeMap& m, int h, const VC& v, double sc) {
@@ -257,19 +257,22 @@ bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vect
             for (int m = 1; m <= len; ++m) pair(cf(shifted(k, l2, m)), cf(shifted(k, l2, -m)));
         }
     };
-    // the mirrored chains k +- m e_{d-2} of a node k (k_{d-2} = 0) whose
-    // children there start in state S2: per m the slots of A_m then B_m
-    auto pair2_chain = [&](const std::vector<int>& k, int S2, const CoefFn& cf) {
-        const int l2 = d - 2;
+    // dimensions in pair form: d-2, d-3, ..., QR_TREE_PAIR_LEVELS of them
+    const int nlv = std::max(0, std::min(QR_TREE_PAIR_LEVELS, d - 2));
+    auto paired = [&](int l2) { return l2 <= d - 2 && l2 >= d - 1 - nlv; };
+    std::function<void(int, int, const std::vector<int>&, const CoefFn&)> node, new_children;
+    // the mirrored chains k +- m e_l2 of a node k (k_l2 = 0) whose children
+    // there start in state S2: per m the slots of A_m then B_m
+    auto pair_chain = [&](int l2, const std::vector<int>& k, int S2, const CoefFn& cf) {
         for (int m = 1, S = S2;; ++m) {
             const std::vector<int> kp = shifted(k, l2, m);
-            const CoefFn ca = [&, m](const std::vector<int>& q) {
+            const CoefFn ca = [&, l2, m](const std::vector<int>& q) {
                 VC v = cf(q);
                 const VC w = cf(shifted(q, l2, -2 * m));
                 v.insert(v.end(), w.begin(), w.end());
                 return v;
             };
-            const CoefFn cb = [&, m](const std::vector<int>& q) {
+            const CoefFn cb = [&, l2, m](const std::vector<int>& q) {
                 VC v = cf(q), w = cf(shifted(q, l2, -2 * m));
                 for (auto& t : v) t.second *= std::complex<double>(0.0, 1.0);
                 for (auto& t : w) v.emplace_back(t.first, t.second * std::complex<double>(0.0, -1.0));
@@ -279,33 +282,36 @@ bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vect
             single(cb(kp));
             if (leaf(l2, S)) break;
             if (new_ok(S)) {
-                last_children(kp, S, ca);
-                last_children(kp, S, cb);
+                new_children(l2, S, kp, ca);
+                new_children(l2, S, kp, cb);
             }
             if (!ext_ok(S)) break;
             S = ext_S(S);
         }
     };
-    std::function<void(int, int, const std::vector<int>&)> node = [&](int L, int S, const std::vector<int>& k) {
-        single(plain(k));
+    // children in the dimensions after L of a node k in state S
+    new_children = [&](int L, int S, const std::vector<int>& k, const CoefFn& cf) {
+        for (int l2 = L + 1; l2 < d; ++l2) {
+            if (leaf(l2, new_S(S))) {
+                pair(cf(shifted(k, l2, 1)), cf(shifted(k, l2, -1)));
+            } else if (l2 == d - 1) {
+                last_children(k, S, cf);
+            } else if (paired(l2)) {
+                pair_chain(l2, k, new_S(S), cf);
+            } else {
+                node(l2, new_S(S), shifted(k, l2, 1), cf);
+                node(l2, new_S(S), shifted(k, l2, -1), cf);
+            }
+        }
+    };
+    node = [&](int L, int S, const std::vector<int>& k, const CoefFn& cf) {
+        single(cf(k));
         if (ext_ok(S)) {
             const std::vector<int> k2 = shifted(k, L, k[L] > 0 ? 1 : -1);
-            if (leaf(L, ext_S(S))) single(plain(k2));
-            else node(L, ext_S(S), k2);
+            if (leaf(L, ext_S(S))) single(cf(k2));
+            else node(L, ext_S(S), k2, cf);
         }
-        if (new_ok(S))
-            for (int l2 = L + 1; l2 < d; ++l2) {
-                if (leaf(l2, new_S(S))) {
-                    pair(plain(shifted(k, l2, 1)), plain(shifted(k, l2, -1)));
-                } else if (l2 == d - 1) {
-                    last_children(k, S, plain);
-                } else if (QR_TREE_PAIR_D2 && l2 == d - 2) {
-                    pair2_chain(k, new_S(S), plain);
-                } else {
-                    node(l2, new_S(S), shifted(k, l2, 1));
-                    node(l2, new_S(S), shifted(k, l2, -1));
-                }
-            }
+        if (new_ok(S)) new_children(L, S, k, cf);
     };
     std::vector<int> zero(d, 0);
     TreeMap r{};
@@ -316,7 +322,7 @@ bool build_tree_map(int kind, int d, int n, const std::vector<int>& K, std::vect
     for (int l = 0; l < d; ++l) {
         const std::vector<int> k = shifted(zero, l, 1);
         if (leaf(l, S0)) single(plain(k));
-        else node(l, S0, k);
+        else node(l, S0, k, plain);
     }
     return ok && emitted == (nG - 1) / 2;
 }

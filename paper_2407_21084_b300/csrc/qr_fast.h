@@ -5,22 +5,24 @@
 
 namespace qr {
 
-// One slot of the tree layout: slot.x = sum_t c[0][t] a[i[0][t]] (t < 4,
-// terms with c = 0 skipped), slot.y likewise with row 1, where a is a master
-// coefficient row seen as 2|Gamma| doubles (re, im interleaved).
-struct TreeMap {
-    int i[2][4];
-    double c[2][4];
-};
-
-// The mirrored chains k +- m e_{d-2} of the second-to-last dimension are
-// evaluated in pair form (one sum and one difference subtree per m against
-// the powers of that dimension's phase) instead of two Horner chains; the
-// device traversal (qr_tree.cuh) and the host layout (build_tree_map)
-// both follow this switch.
-#ifndef QR_TREE_PAIR_D2
-#define QR_TREE_PAIR_D2 1
+// The mirrored chains k +- m e_l of the dimensions l = d-2, d-3, ..., (this
+// many, at most d-2 of them) are evaluated in pair form (one sum and one
+// difference subtree per m against the powers of that dimension's phase)
+// instead of two Horner chains; the device traversal (qr_tree.cuh) and the
+// host layout (build_tree_map) both follow this setting.
+#ifndef QR_TREE_PAIR_LEVELS
+#define QR_TREE_PAIR_LEVELS 2
 #endif
+
+// One slot of the tree layout: slot.x = sum_t c[0][t] a[i[0][t]] (terms with
+// c = 0 skipped), slot.y likewise with row 1, where a is a master coefficient
+// row seen as 2|Gamma| doubles (re, im interleaved). Each pair level doubles
+// the coefficients a slot can combine.
+constexpr int kTreeTerms = 2 << QR_TREE_PAIR_LEVELS;
+struct TreeMap {
+    int i[2][kTreeTerms];
+    double c[2][kTreeTerms];
+};
 
 // number of slots of the compiled tree for (kind, d, n); 0 if not compiled
 int tree_slots(int kind, int d, int n);

@@ -324,14 +324,19 @@ long long qr_mlp_num_params(const qr_mlp* m) { return m ? (long long)m->n_params
 qr_status qr_mlp_get_params(const qr_mlp* m, float* out)
 {
     if (!m || !out) return QR_EINVAL;
-    if (cudaMemcpy(out, m->d_params, 4 * m->n_params, cudaMemcpyDeviceToHost) != cudaSuccess) return QR_ECUDA;
+    // ordered after the work queued on the network's stream
+    if (cudaMemcpyAsync(out, m->d_params, 4 * m->n_params, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess)
+        return QR_ECUDA;
     return QR_OK;
 }
 
 qr_status qr_mlp_set_params(qr_mlp* m, const float* in)
 {
     if (!m || !in) return QR_EINVAL;
-    if (cudaMemcpy(m->d_params, in, 4 * m->n_params, cudaMemcpyHostToDevice) != cudaSuccess) return QR_ECUDA;
+    if (cudaMemcpyAsync(m->d_params, in, 4 * m->n_params, cudaMemcpyHostToDevice, m->stream) != cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess)
+        return QR_ECUDA;
     return QR_OK;
 }
 
@@ -349,7 +354,9 @@ qr_status qr_mlp_gradients(qr_mlp* m, const float* X, const float* T, int B, flo
     qr_status s = forward(m, X, B, nullptr);
     if (s == QR_OK) s = backward(m, X, T, B, loss_out);
     if (s != QR_OK) return s;
-    if (grad_out && cudaMemcpy(grad_out, m->d_grad, 4 * m->n_params, cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (grad_out && (cudaMemcpyAsync(grad_out, m->d_grad, 4 * m->n_params, cudaMemcpyDeviceToHost, m->stream) !=
+                         cudaSuccess ||
+                     cudaStreamSynchronize(m->stream) != cudaSuccess))
         return mfail(m, QR_ECUDA, "copy gradients");
     return QR_OK;
 }

@@ -73,7 +73,7 @@ __device__ __forceinline__ V2<R> tree_slot(const double* a, const TreeMap& mp)
     for (int h = 0; h < 2; ++h) {
         double t = 0.0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < kTreeTerms; ++u)
             if (mp.c[h][u] != 0) t += mp.c[h][u] * a[mp.i[h][u]];
         v[h] = t;
     }

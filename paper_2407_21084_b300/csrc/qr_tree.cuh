@@ -63,13 +63,15 @@ struct TreeShape {
 
 // the phases of one path point as the tree evaluation sees them: z[p][l] =
 // e^{2 pi i F(x_l)}, the powers zl[p][m] = z[p][D-1]^{m+1} and, for the pair
-// form of the second-to-last dimension, zk[p][m] = z[p][D-2]^{m+1}
+// form of dimension l = D-2-v (v < NLV), zk[p][v][m] = z[p][l]^{m+1}
 template <typename R, int P, int D, int NPW>
 struct TreePh {
-    static constexpr int NK = (QR_TREE_PAIR_D2 && D >= 3) ? NPW : 1;
+    static constexpr int NLV = D - 2 < QR_TREE_PAIR_LEVELS ? (D > 2 ? D - 2 : 0) : QR_TREE_PAIR_LEVELS;
+    // dimension L2 (>= 1, a new-dimension child) takes the pair form
+    static constexpr bool paired(int L2) { return L2 <= D - 2 && L2 >= D - 1 - NLV; }
     V2<R> z[P][D];
     V2<R> zl[P][NPW];
-    V2<R> zk[P][NK];
+    V2<R> zk[P][NLV > 0 ? NLV : 1][NPW];
 };
 
 template <typename R>
@@ -369,21 +371,21 @@ __device__ __forceinline__ void rs_acc(V2<R>& T, V2<R> A, V2<R> B, V2<R> w)
 template <typename R, int D, int NN, int KIND, int P, int L2, int S>
 struct NewDims;
 
-// The + and - chains k +- m e_{D-2} of the second-to-last dimension below a
-// node (position MM = m - 1 of the chain, node state S2). With U+-_m the
-// subtree values at k +- m e_{D-2} without their extensions (both in the
-// last dimension's phase) the chains contribute
+// The + and - chains k +- m e_L of a paired dimension L below a node
+// (position MM = m - 1 of the chain, node state S2). With U+-_m the subtree
+// values at k +- m e_L without their extensions (both in the phases of the
+// later dimensions) the chains contribute
 //   sum_m (w^m U+_m + conj(w)^m U-_m) = sum_m (Re(w^m) A_m + Im(w^m) B_m),
 // A_m = U+_m + U-_m, B_m = i (U+_m - U-_m), both evaluated as subtrees of
 // the same shape from pre-combined coefficients; each mirrored pair of
 // nodes then costs 4 FMA against the powers w^m instead of two Horner edges.
-template <typename R, int D, int NN, int KIND, int P, int S2, int MM>
-struct Pair2Chain {
+template <typename R, int D, int NN, int KIND, int P, int L, int S2, int MM>
+struct PairChain {
     using Sh = TreeShape<D, NN, KIND>;
     using Ph = TreePh<R, P, D, Sh::npow()>;
     static __device__ __forceinline__ void run(const V2<R>* __restrict__ c, int& off, V2<R> (&T)[P], const Ph& z)
     {
-        static_assert(MM < Ph::NK, "power table too short");
+        static_assert(MM < Sh::npow(), "power table too short");
         V2<R> A[P], B[P];
         const V2<R> ca = c[off], cb = c[off + 1];
         off += 2;
@@ -392,14 +394,14 @@ struct Pair2Chain {
             A[p] = ca;
             B[p] = cb;
         }
-        if constexpr (!Sh::leaf(D - 2, S2) && Sh::new_ok(S2)) {
-            NewDims<R, D, NN, KIND, P, D - 1, S2>::run(c, off, A, z);
-            NewDims<R, D, NN, KIND, P, D - 1, S2>::run(c, off, B, z);
+        if constexpr (!Sh::leaf(L, S2) && Sh::new_ok(S2)) {
+            NewDims<R, D, NN, KIND, P, L + 1, S2>::run(c, off, A, z);
+            NewDims<R, D, NN, KIND, P, L + 1, S2>::run(c, off, B, z);
         }
 #pragma unroll
-        for (int p = 0; p < P; ++p) rs_acc<R>(T[p], A[p], B[p], z.zk[p][MM]);
-        if constexpr (!Sh::leaf(D - 2, S2) && Sh::ext_ok(S2))
-            Pair2Chain<R, D, NN, KIND, P, Sh::ext_S(S2), MM + 1>::run(c, off, T, z);
+        for (int p = 0; p < P; ++p) rs_acc<R>(T[p], A[p], B[p], z.zk[p][D - 2 - L][MM]);
+        if constexpr (!Sh::leaf(L, S2) && Sh::ext_ok(S2))
+            PairChain<R, D, NN, KIND, P, L, Sh::ext_S(S2), MM + 1>::run(c, off, T, z);
     }
 };
 
@@ -432,8 +434,8 @@ struct NewDims {
                     for (int p = 0; p < P; ++p) pair_acc<R>(T[p], ac, be, z.zl[p][mm]);
                 }
                 off += 2 * len;
-            } else if constexpr (QR_TREE_PAIR_D2 && L2 == D - 2) {
-                Pair2Chain<R, D, NN, KIND, P, S2, 0>::run(c, off, T, z);
+            } else if constexpr (Ph::paired(L2)) {
+                PairChain<R, D, NN, KIND, P, L2, S2, 0>::run(c, off, T, z);
             } else {
                 constexpr int sz = Sh::size(L2, S2);
                 const V2<R>* cs = c + off;
@@ -544,10 +546,12 @@ __device__ __forceinline__ void tree_series(const V2<R>* __restrict__ c, const V
         ph.zl[p][0] = z[p][D - 1];
 #pragma unroll
         for (int m = 1; m < Sh::npow(); ++m) ph.zl[p][m] = cmul<R>(ph.zl[p][m - 1], z[p][D - 1]);
-        if constexpr (QR_TREE_PAIR_D2 && D >= 3) {
-            ph.zk[p][0] = z[p][D - 2];
 #pragma unroll
-            for (int m = 1; m < decltype(ph)::NK; ++m) ph.zk[p][m] = cmul<R>(ph.zk[p][m - 1], z[p][D - 2]);
+        for (int v = 0; v < decltype(ph)::NLV; ++v) {
+            const V2<R> w = z[p][D - 2 - v];
+            ph.zk[p][v][0] = w;
+#pragma unroll
+            for (int m = 1; m < Sh::npow(); ++m) ph.zk[p][v][m] = cmul<R>(ph.zk[p][v][m - 1], w);
         }
     }
     V2<R> T[P];

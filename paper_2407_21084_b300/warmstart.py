@@ -32,11 +32,18 @@ class MLP:
     """FP32 multilayer perceptron living in libqrmc (qr_mlp_*)."""
 
     def __init__(self, n_in, n_out, width=256, depth=3, max_batch=1024, seed=5, stream=None):
+        """stream: a torch.cuda.Stream; default the current stream. The
+        library's kernels and the binding's own tensor work (batch gathers,
+        copies) both run on it, in order."""
+        import torch
+
         self._L = L.load()
         self.n_in, self.n_out, self.max_batch = n_in, n_out, max_batch
         self.dims = [n_in] + [width] * depth + [n_out]
+        self._ts = stream if stream is not None else torch.cuda.current_stream()
         self._h = C.c_void_p()
-        st = self._L.qr_mlp_create(C.byref(self._h), n_in, width, depth, n_out, max_batch, seed, stream)
+        st = self._L.qr_mlp_create(C.byref(self._h), n_in, width, depth, n_out, max_batch, seed,
+                                   C.c_void_p(self._ts.cuda_stream))
         if st != L.QR_OK:
             msg = self._L.qr_mlp_last_error(self._h).decode() if self._h else ""
             self.close()
@@ -71,6 +78,12 @@ class MLP:
 
     def gradients(self, X, T):
         """Gradient of mean((y - T)^2) on raw (unstandardised) arrays."""
+        import torch
+
+        with torch.cuda.stream(self._ts):
+            return self._gradients(X, T)
+
+    def _gradients(self, X, T):
         x, t = self._dev(X), self._dev(T)
         g = np.zeros(self.num_params, dtype=np.float32)
         loss = C.c_float()
@@ -79,6 +92,12 @@ class MLP:
         return g, float(loss.value)
 
     def forward_raw(self, X) -> np.ndarray:
+        import torch
+
+        with torch.cuda.stream(self._ts):
+            return self._forward_raw(X)
+
+    def _forward_raw(self, X) -> np.ndarray:
         import torch
 
         x = self._dev(X)
@@ -94,6 +113,12 @@ class MLP:
         coefficients decide the sup error of the series; the small ones are
         mostly Monte Carlo noise of the training solves); "per_output"
         standardises each output on its own."""
+        import torch
+
+        with torch.cuda.stream(self._ts):
+            return self._fit(X, Y, steps, batch, lr, seed, lr_final, target_scale)
+
+    def _fit(self, X, Y, steps, batch, lr, seed, lr_final, target_scale):
         import torch
 
         X = np.asarray(X, dtype=np.float64)

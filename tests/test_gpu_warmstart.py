@@ -51,6 +51,28 @@ def test_training_fits_a_smooth_map(ws):
     assert err < 0.1
 
 
+def test_training_on_a_side_stream_equals_the_default_stream(ws):
+    """The network runs on the torch stream current at its creation; trained
+    there (a non-blocking stream whose batch gathers the library's kernels
+    must wait for) it reaches exactly the parameters of the same training on
+    the default stream."""
+    import torch
+
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-1, 1, size=(1024, 5))
+    Y = np.column_stack([np.sin(X @ rng.normal(size=5)), X[:, 0] * X[:, 1]])
+    params = []
+    for side in (False, True):
+        st = torch.cuda.Stream() if side else torch.cuda.default_stream()
+        with torch.cuda.stream(st):
+            net = ws.MLP(5, 2, width=64, depth=3, max_batch=256, seed=6)
+            net.fit(X, Y, steps=300, batch=256, lr=3e-3)
+            params.append(net.get_params())
+            assert np.isfinite(net.predict(X[:64])).all()
+            net.close()
+    assert np.array_equal(params[0], params[1])
+
+
 def test_rows_round_trip(ws):
     rng = np.random.default_rng(2)
     K = np.array([[a, b] for a in range(-2, 3) for b in range(-2, 3)])
