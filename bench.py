@@ -470,7 +470,7 @@ def _kernel_hash() -> str:
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("qr_fast.cu", "qr_tree.cuh", "qr_device.cuh", "qr_internal.h"):
+    for f in ("qr_fast.cu", "qr_fast.h", "qr_tree.cuh", "qr_device.cuh", "qr_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2407_21084_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
