@@ -256,6 +256,28 @@ qr_status qr_test_points(const qr_ctx* ctx, int i, long long n, double* x_out);
  * mechanism. */
 qr_status qr_selftest_wait_timeout(qr_ctx* ctx);
 
+/* Host-side fault injection (the paper has no counterpart): arms one fault
+ * on the context, taken once by the next call that reaches it, so that the
+ * library's failure paths run without faulting the GPU:
+ *   QR_FAULT_ALLOC   the context's next device allocation fails: that call
+ *                    returns QR_ENOMEM (qr_init, qr_eval with host points,
+ *                    qr_shard, qr_batch_create, ...);
+ *   QR_FAULT_LAUNCH  the next qr_picard_step / qr_backward_sweep returns
+ *                    QR_ECUDA before it launches anything;
+ *   QR_FAULT_NAN     the next qr_picard_step / qr_backward_sweep first sets
+ *                    the k = 0 coefficient of row N-1 to NaN (master row and
+ *                    packed copies, the context's own buffers), so that the
+ *                    path kernel's non-finite guard makes the call return
+ *                    QR_ENONFINITE; qr_set_coefs then restores a state (with
+ *                    N = 1 no series reads a coefficient row and the call
+ *                    succeeds).
+ * QR_FAULT_NONE disarms. The environment variable QR_FAULT = alloc, launch
+ * or nan arms the same fault on every context at qr_init. A batch's
+ * iteration (qr_batch_picard_step) does not take the iteration faults.
+ * QR_EINVAL for a NULL context or an unknown kind. */
+enum { QR_FAULT_NONE = 0, QR_FAULT_ALLOC = 1, QR_FAULT_LAUNCH = 2, QR_FAULT_NAN = 3 };
+qr_status qr_inject_fault(qr_ctx* ctx, int kind);
+
 /* ---- many instances in one iteration ----------------------------------
  * A batch advances n contexts (created by qr_init with QR_FP32, sharing one
  * stream, each with one of the compiled index-set classes: |k|_inf <= 4 in

@@ -16,6 +16,7 @@ QR_OK, QR_EINVAL, QR_ENOMEM, QR_ECUDA, QR_ETIMEOUT, QR_ENONFINITE, QR_ENOTIMPL =
 QR_NU_LOMAX, QR_NU_STUDENT2, QR_NU_CAUCHY = range(3)
 QR_G_LINF, QR_G_L1, QR_G_HYP, QR_G_FULL_N, QR_G_TOTAL_N, QR_G_HYP_N = range(6)
 QR_F_ZERO, QR_F_LINEAR, QR_F_CUBIC_MANUF, QR_F_PAPER_MIN = range(4)
+QR_FAULT_NONE, QR_FAULT_ALLOC, QR_FAULT_LAUNCH, QR_FAULT_NAN = range(4)
 QR_GT_COS, QR_GT_TRIGPOLY, QR_GT_PAPER_SIN = range(3)
 QR_FP64, QR_FP32 = 0, 1
 QR_U_PHILOX, QR_U_LATTICE = 0, 1
@@ -28,6 +29,7 @@ EXPORTS = [
     "qr_get_coefs", "qr_set_coefs", "qr_get_responses", "qr_set_profiling", "qr_get_stats",
     "qr_last_error", "qr_status_string", "qr_destroy", "qr_philox_words", "qr_sample", "qr_sample_normals_tree", "qr_project_static", "qr_test_points",
     "qr_selftest_wait_timeout",
+    "qr_inject_fault",
     "qr_mlp_create", "qr_mlp_num_params", "qr_mlp_get_params", "qr_mlp_set_params", "qr_mlp_forward",
     "qr_mlp_gradients", "qr_mlp_train_step", "qr_mlp_last_error", "qr_mlp_destroy",
     "qr_batch_create", "qr_batch_picard_step", "qr_batch_info", "qr_batch_set_grouping", "qr_batch_groups",
@@ -197,6 +199,8 @@ def load(path: str | None = None):
     L.qr_batch_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
     L.qr_selftest_wait_timeout.restype = C.c_int
     L.qr_selftest_wait_timeout.argtypes = [vp]
+    L.qr_inject_fault.restype = C.c_int
+    L.qr_inject_fault.argtypes = [vp, C.c_int]
     L.qr_batch_set_grouping.restype = C.c_int
     L.qr_batch_set_grouping.argtypes = [vp, C.c_int]
     L.qr_batch_groups.restype = C.c_int

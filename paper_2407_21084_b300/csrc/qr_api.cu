@@ -4,12 +4,15 @@
 #include <map>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <complex>
 #include <functional>
 #include <new>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "qr_batch.h"
 #include "qr_cosine.h"
@@ -56,6 +59,7 @@ struct qr_ctx {
     void (*dev_free)(void*, void*, void*) = nullptr;
     void* alloc_user = nullptr;
     bool coefs_changed = true;  // by qr_set_coefs since a batch last packed its group blocks
+    int fault = QR_FAULT_NONE;  // armed host-side fault (qr_inject_fault), taken once
     double2* d_gsum = nullptr;  // kShardGroups x N x |Gamma_+|
     // cosine basis on N^d (Lemma ortho:dim1), run as the unfolded Z^d set
     // with half-angle phases; raw projections are symmetrised over the sign
@@ -390,6 +394,10 @@ bool build_proj_perm(int kind, int d, int n, const std::vector<int>& K, int zero
 // stream-ordered allocation on the context's stream
 void* ctx_malloc(qr_ctx* c, size_t bytes)
 {
+    if (c->fault == QR_FAULT_ALLOC) {
+        c->fault = QR_FAULT_NONE;
+        return nullptr;
+    }
     bytes = bytes < 16 ? 16 : bytes;
     if (c->dev_alloc) return c->dev_alloc(bytes, c->stream, c->alloc_user);
     void* q = nullptr;
@@ -612,6 +620,11 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     *out = nullptr;
     qr_ctx* c = new (std::nothrow) qr_ctx();
     if (!c) return QR_ENOMEM;
+    if (const char* fe = std::getenv("QR_FAULT")) {
+        if (!std::strcmp(fe, "alloc")) c->fault = QR_FAULT_ALLOC;
+        else if (!std::strcmp(fe, "launch")) c->fault = QR_FAULT_LAUNCH;
+        else if (!std::strcmp(fe, "nan")) c->fault = QR_FAULT_NAN;
+    }
     auto bail = [&](qr_status s, const std::string& m) {
         // keep the context so that the caller can read the message, but no
         // device state: the caller must still qr_destroy it
@@ -1053,12 +1066,68 @@ void qr_destroy(qr_ctx* ctx)
 
 static bool ready(const qr_ctx* c) { return c && c->d_packed; }
 
+// NVTX range over a host call (shows the enqueue of the iterations on a
+// profiler's timeline; no cost when no tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+// every packed copy of the master coefficient rows, rebuilt from d_alpha
+static qr_status repack_all(qr_ctx* ctx)
+{
+    ctx->coefs_changed = true;
+    if (ctx->cos_direct)
+        QR_CU(ctx, launch_pack_cos(ctx->prec, ctx->d_alpha, ctx->nG, ctx->d_cpos, ctx->d_packed, ctx->row_stride,
+                                   ctx->N, ctx->stream));
+    else
+        QR_CU(ctx, launch_pack(ctx->prec, ctx->P, ctx->d_alpha, ctx->nG, ctx->zero_idx, ctx->d_packed,
+                               ctx->row_stride, ctx->N, ctx->stream));
+    if (ctx->tree_slots) QR_CU(ctx, pack_tree_rows(ctx, 0, ctx->N));
+    return QR_OK;
+}
+
+// the faults an iteration takes at its start (qr_inject_fault)
+static qr_status take_iteration_fault(qr_ctx* ctx)
+{
+    const int f = ctx->fault;
+    if (f == QR_FAULT_LAUNCH) {
+        ctx->fault = QR_FAULT_NONE;
+        return fail(ctx, QR_ECUDA, "injected launch failure (nothing was launched)");
+    }
+    if (f == QR_FAULT_NAN) {
+        ctx->fault = QR_FAULT_NONE;
+        if (ctx->N < 2) return QR_OK;  // no coefficient row is read by a series
+        // the k = 0 coefficient of the last row becomes NaN in the master row
+        // and every packed copy: every series evaluated at t_{N-1} is NaN
+        const int k0 = ctx->cos_direct ? 0 : ctx->zero_idx;
+        const double2 bad = make_double2(std::nan(""), 0.0);
+        QR_CU(ctx, cudaMemcpyAsync(ctx->d_alpha + (size_t)(ctx->N - 1) * ctx->nG + k0, &bad, sizeof bad,
+                                   cudaMemcpyHostToDevice, ctx->stream));
+        QR_CU(ctx, cudaStreamSynchronize(ctx->stream));
+        return repack_all(ctx);
+    }
+    return QR_OK;
+}
+
+qr_status qr_inject_fault(qr_ctx* ctx, int kind)
+{
+    if (!ctx || kind < QR_FAULT_NONE || kind > QR_FAULT_NAN) return QR_EINVAL;
+    ctx->fault = kind;
+    return QR_OK;
+}
+
 qr_status qr_picard_step(qr_ctx* ctx, int n_iter, double* residual_out)
 {
     if (!ready(ctx)) return QR_EINVAL;
     if (ctx->shard_world > 1)
         return fail(ctx, QR_EINVAL, "qr_picard_step: a sharded context iterates by qr_picard_begin/finish");
     if (n_iter < 0) return fail(ctx, QR_EINVAL, "n_iter must be >= 0");
+    NvtxRange range("qr_picard_step");
+    if (n_iter > 0) {
+        qr_status fs = take_iteration_fault(ctx);
+        if (fs != QR_OK) return fs;
+    }
     QR_CU(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
     if (!ctx->profiling && !ctx->graph && !ctx->graph_failed && n_iter > 0) {
         // capture one iteration; streams that cannot be captured (the legacy
@@ -1081,6 +1150,7 @@ qr_status qr_picard_step(qr_ctx* ctx, int n_iter, double* residual_out)
         }
     }
     for (int q = 0; q < n_iter; ++q) {
+        NvtxRange it_range("picard iteration");
         if (ctx->graph && !ctx->profiling) {
             QR_CU(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
         } else {
@@ -1209,6 +1279,9 @@ qr_status qr_backward_sweep(qr_ctx* ctx)
 {
     if (!ready(ctx)) return QR_EINVAL;
     if (ctx->shard_world > 1) return fail(ctx, QR_EINVAL, "qr_backward_sweep: not for a sharded context");
+    NvtxRange range("qr_backward_sweep");
+    qr_status fs = take_iteration_fault(ctx);
+    if (fs != QR_OK) return fs;
     QR_CU(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
     for (int i = ctx->N - 1; i >= 0; --i) {
         qr_status s = run_rows(ctx, i, i + 1);
@@ -1318,14 +1391,8 @@ qr_status qr_set_coefs(qr_ctx* ctx, const double* alpha_in)
     }
     QR_CU(ctx, cudaMemcpyAsync(ctx->d_alpha, src, sizeof(double2) * (size_t)ctx->N * ctx->nG,
                                cudaMemcpyHostToDevice, ctx->stream));
-    ctx->coefs_changed = true;
-    if (ctx->cos_direct)
-        QR_CU(ctx, launch_pack_cos(ctx->prec, ctx->d_alpha, ctx->nG, ctx->d_cpos, ctx->d_packed, ctx->row_stride,
-                                   ctx->N, ctx->stream));
-    else
-        QR_CU(ctx, launch_pack(ctx->prec, ctx->P, ctx->d_alpha, ctx->nG, ctx->zero_idx, ctx->d_packed,
-                               ctx->row_stride, ctx->N, ctx->stream));
-    if (ctx->tree_slots) QR_CU(ctx, pack_tree_rows(ctx, 0, ctx->N));
+    qr_status s = repack_all(ctx);
+    if (s != QR_OK) return s;
     QR_CU(ctx, cudaStreamSynchronize(ctx->stream));
     return QR_OK;
 }

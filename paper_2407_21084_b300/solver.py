@@ -6,6 +6,8 @@ the CUDA stream the library launches on; all arithmetic runs in libqrmc.
 from __future__ import annotations
 
 import ctypes as C
+import json
+import time
 
 import numpy as np
 
@@ -34,6 +36,14 @@ class Solver:
         fp = np.ascontiguousarray(np.atleast_1d(f_par), dtype=np.float64)
         gp = np.ascontiguousarray(np.atleast_1d(g_par), dtype=np.float64)
         self._keep = (b, sigma, fp, gp)
+        # the problem as constructed (a checkpoint stores it beside the coefficients)
+        self._config = dict(d=int(d), N=int(N), T=float(T), nu_kind=int(nu_kind), mu=float(mu),
+                            gamma_kind=int(gamma_kind), gamma_n=int(gamma_n), b=b.tolist(), sigma=sigma.tolist(),
+                            f_kind=int(f_kind), f_par=fp.tolist(), g_kind=int(g_kind), g_par=gp.tolist(), M=int(M),
+                            seed=int(seed), precision=int(precision), clamp_L=float(clamp_L),
+                            lattice_n=int(lattice_n), instance=int(instance), path_kernel=int(path_kernel),
+                            damping_q=float(damping_q))
+        self.iterations_done = 0  # Picard iterations (or sweeps) behind the current coefficients
         nu = L.QrNu(nu_kind, mu)
         gam = L.QrGamma(gamma_kind, gamma_n)
         f = L.QrFn(f_kind, _dp(fp), fp.size)
@@ -92,10 +102,72 @@ class Solver:
     def picard_step(self, n_iter: int = 1) -> float:
         r = C.c_double()
         L.check(self._L.qr_picard_step(self._ctx, n_iter, C.byref(r)), self._ctx)
+        self.iterations_done += n_iter
         return r.value
 
     def backward_sweep(self):
         L.check(self._L.qr_backward_sweep(self._ctx), self._ctx)
+        self.iterations_done += self.N
+
+    def evals_per_iteration(self) -> int:
+        """path.coef evaluations of one Picard iteration: M |Gamma| N(N+1)/2."""
+        return self.M * self.nG * self.N * (self.N + 1) // 2
+
+    def iterate(self, n_iter: int, log=None, tol: float | None = None) -> list:
+        """Picard iterations one at a time with a metrics record each: wall
+        seconds (the step waits for its device work), path.coef evaluations
+        per second, the residual max |alpha^(q) - alpha^(q-1)|, and the clamp
+        hits and non-finite responses of that iteration. Records are appended
+        to `log` (a path or a text file object) as JSON lines. Stops early
+        once the residual is <= tol."""
+        out = []
+        fh = open(log, "a") if isinstance(log, str) else log
+        try:
+            for _ in range(n_iter):
+                before = self.stats()
+                t0 = time.perf_counter()
+                r = self.picard_step(1)
+                sec = time.perf_counter() - t0
+                after = self.stats()
+                rec = {"iteration": self.iterations_done, "seconds": sec,
+                       "path_coef_evals_per_s": self.evals_per_iteration() / sec, "residual": r,
+                       "clamp_hits": after["clamp_hits"] - before["clamp_hits"],
+                       "nonfinite": after["nonfinite"] - before["nonfinite"]}
+                out.append(rec)
+                if fh is not None:
+                    fh.write(json.dumps(rec) + "\n")
+                    fh.flush()
+                if tol is not None and r <= tol:
+                    break
+        finally:
+            if isinstance(log, str):
+                fh.close()
+        return out
+
+    # ------------------------------------------------------- checkpoints
+    def save_checkpoint(self, path: str):
+        """The Picard state (the FP64 coefficient rows, the iterations behind
+        them and the problem as constructed) to an .npz file. The iteration is
+        a function of the previous coefficients and of counter-based random
+        numbers that do not depend on the iteration, so a solver resumed from
+        the file continues bit-identically."""
+        np.savez(path, coefs=self.coefs(), iterations=np.int64(self.iterations_done),
+                 config=np.array(json.dumps(self._config)))
+
+    @classmethod
+    def load_checkpoint(cls, path: str, stream=None) -> "Solver":
+        z = np.load(path)
+        cfg = json.loads(str(z["config"]))
+        cfg["b"] = np.asarray(cfg["b"])
+        cfg["sigma"] = np.asarray(cfg["sigma"])
+        s = cls(**cfg, stream=stream)
+        s.set_coefs(z["coefs"])
+        s.iterations_done = int(z["iterations"])
+        return s
+
+    def inject_fault(self, kind: int):
+        """Arm one host-side fault (L.QR_FAULT_ALLOC, _LAUNCH, _NAN; see qr_inject_fault)."""
+        L.check(self._L.qr_inject_fault(self._ctx, int(kind)), self._ctx)
 
     def coefs(self) -> np.ndarray:
         a = np.zeros((self.N, self.nG), dtype=np.complex128)

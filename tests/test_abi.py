@@ -77,6 +77,40 @@ def test_host_validation_rejects_before_any_device_work(lib, kw, frag):
     assert frag in msg
 
 
+def test_fault_injection_validates_without_a_device(lib):
+    import ctypes as C
+
+    from paper_2407_21084_b300 import _lib as L
+
+    assert lib.qr_inject_fault(None, L.QR_FAULT_ALLOC) == L.QR_EINVAL
+    # a context kept for its message by a refused qr_init still takes a fault kind
+    st, ctx = _init_keep(lib, d=0)
+    try:
+        assert st == L.QR_EINVAL and ctx
+        assert lib.qr_inject_fault(ctx, 9) == L.QR_EINVAL
+        assert lib.qr_inject_fault(ctx, L.QR_FAULT_NAN) == L.QR_OK
+        assert lib.qr_inject_fault(ctx, L.QR_FAULT_NONE) == L.QR_OK
+    finally:
+        lib.qr_destroy(ctx)
+
+
+def _init_keep(lib, d):
+    import ctypes as C
+
+    from paper_2407_21084_b300 import _lib as L
+
+    b = np.zeros(1)
+    sig = np.eye(1).ravel()
+    par = np.ones(4)
+    ctx = C.c_void_p()
+    st = lib.qr_init(C.byref(ctx), d, 4, 1.0, C.byref(L.QrNu(0, 3.0)), C.byref(L.QrGamma(1, 2)),
+                     b.ctypes.data_as(C.POINTER(C.c_double)), sig.ctypes.data_as(C.POINTER(C.c_double)),
+                     C.byref(L.QrFn(0, par.ctypes.data_as(C.POINTER(C.c_double)), 4)),
+                     C.byref(L.QrFn(0, par.ctypes.data_as(C.POINTER(C.c_double)), 4)),
+                     C.byref(L.QrOpts(64, 1, 0, 0.0, None, 0, 0, 0, 0)))
+    return st, ctx
+
+
 def test_status_strings(lib):
     assert lib.qr_status_string(0) == b"ok"
     assert lib.qr_status_string(4) == b"device wait timed out"
