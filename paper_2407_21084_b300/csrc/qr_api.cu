@@ -454,6 +454,10 @@ qr_status check_device_status(qr_ctx* c)
     c->stats.clamp_hits = (long long)c->h_counters[CNT_CLAMP];
     c->stats.nonfinite = (long long)c->h_counters[CNT_NONFINITE];
     if (st & ST_TIMEOUT) return fail(c, QR_ETIMEOUT, "a bounded wait for a bulk copy ran out on the device");
+    if (st & ST_BOUNDS) {
+        cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+        return fail(c, QR_ECUDA, "checked build: a kernel index fell outside its buffer (the access was skipped)");
+    }
     return QR_OK;
 }
 
@@ -938,6 +942,7 @@ qr_status qr_init(qr_ctx** out, int d, int N, double T, const qr_nu* nu, const q
     }
     if ((s = dalloc(c, &c->d_counters, sizeof(unsigned long long) * CNT_N)) != QR_OK) return bail(s, c->err);
     if ((s = dalloc(c, &c->d_status, sizeof(unsigned))) != QR_OK) return bail(s, c->err);
+    P.check = c->d_status;
     if (cudaMallocHost(&c->h_counters, sizeof(unsigned long long) * CNT_N) != cudaSuccess)
         return bail(QR_ENOMEM, "pinned host allocation failed");
     for (auto& e : c->ev)

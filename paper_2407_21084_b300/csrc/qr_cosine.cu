@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(kCosBS, sizeof(R) == 4 ? 4 : 2) k_paths_cos(co
     const R Sv = damp ? (gN + sum) * (R)exp((double)-lw0) : gN + sum;
     unsigned long long bad = 0;
     if (active) {
-        S[(size_t)(i - i_lo) * (size_t)P.M + (size_t)m] = Sv;
+        if (in_bounds(P, i - i_lo >= 0 && i - i_lo < P.N)) S[(size_t)(i - i_lo) * (size_t)P.M + (size_t)m] = Sv;
         if (!isfinite(Sv)) bad = 1;
     } else {
         hits = 0;
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(kCosBS, PPL == 2 ? 3 : (sizeof(R) == 4 ? 4 : 2
         for (int u = 0; u < PPL; ++u) {
             const long long m = (long long)ch * P.chunk + (long long)(r * PPL + u) * BS + tid;
             const bool active = m < P.M;
-            Sv[u] = active ? S[(size_t)ii * (size_t)P.M + (size_t)m] : (R)0;
+            Sv[u] = active && in_bounds(P, ii >= 0 && ii < P.N) ? S[(size_t)ii * (size_t)P.M + (size_t)m] : (R)0;
             V2<R> ph[D];
             start_phases_dev<R, D>(P, i, active ? m : 0, ph);  // e^{i pi U^m} (half angle)
             Wk[u].init(ph, Sv[u]);
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(kCosBS, PPL == 2 ? 3 : (sizeof(R) == 4 ? 4 : 2
     for (int q = tid; q < npos; q += BS) {
         double s = 0.0;
         for (int w = 0; w < W; ++w) s += (double)wacc[(size_t)w * KT + q];
-        out[q] = s;
+        if (in_bounds(P, ii >= 0 && ii < P.N && ch >= 0 && ch < P.n_chunks && gs * 4 + q < row_stride)) out[q] = s;
     }
 }
 

@@ -14,7 +14,29 @@
 
 #include "qr_internal.h"
 
+// Checked builds (QR_CHECKED = 1; build.py --checked, libqrmc_checked.so)
+// stand in for a memory checker: every kernel index into S, the projection
+// partials and the coefficient rows is tested against its buffer; one that
+// falls outside sets ST_BOUNDS in the context's status word (the call then
+// returns QR_ECUDA) and the access is skipped. In normal builds the test
+// folds away.
+#ifndef QR_CHECKED
+#define QR_CHECKED 0
+#endif
+
 namespace qr {
+
+__device__ __forceinline__ bool in_bounds(const QrParams& P, bool ok)
+{
+#if QR_CHECKED
+    if (!ok && P.check) atomicOr(P.check, ST_BOUNDS);
+    return ok;
+#else
+    (void)P;
+    (void)ok;
+    return true;
+#endif
+}
 
 template <typename R> struct V2t;
 template <> struct V2t<float> { using T = float2; };

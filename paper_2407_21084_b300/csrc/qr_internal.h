@@ -15,7 +15,9 @@ constexpr int kNMax = 256;  // time steps
 enum { QR_TAG_START = 0, QR_TAG_INCR = 1, QR_TAG_TEST = 2 };
 
 // device status bits
-enum : unsigned { ST_TIMEOUT = 1u };
+// status word bits: a bounded wait ran out; (checked builds) an index fell
+// outside its buffer and the access was skipped
+enum : unsigned { ST_TIMEOUT = 1u, ST_BOUNDS = 2u };
 
 // counters[0] = clamp hits, counters[1] = non-finite responses,
 // counters[2] = residual (bits of a non-negative double, atomicMax)
@@ -72,6 +74,7 @@ struct QrParams {
     int c_lo, c_hi;  // chunks this context simulates and projects (a shard of paths; all by default)
     int half_angle;  // cosine basis: phases e^{i pi F(x)} instead of e^{2 pi i F(x)}
     double q_damp;   // damping exponent q of eq. (yqi); 0: none
+    unsigned* check; // the context's status word (bounds checks of checked builds)
 };
 
 // The cross-chunk sum of the projection is taken in two fixed levels: the

@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(BS) k_paths(const __grid_constant__ QrParams P
     const R Sv = damp ? (gN + sum) * (R)exp((double)-lw0) : gN + sum;
     unsigned long long bad = 0;
     if (active) {
-        S[(size_t)(i - i_lo) * (size_t)P.M + (size_t)m] = Sv;
+        if (in_bounds(P, i - i_lo >= 0 && i - i_lo < P.N)) S[(size_t)(i - i_lo) * (size_t)P.M + (size_t)m] = Sv;
         if (!isfinite(Sv)) bad = 1;
     } else {
         hits = 0;
@@ -299,7 +299,9 @@ __global__ void __launch_bounds__(BS) k_project(const __grid_constant__ QrParams
         for (int r = 0; r < rounds; ++r) {
             const long long m = (long long)ch * P.chunk + (long long)r * BS + tid;
             const bool active = m < P.M;
-            const R Sv = active ? S[(size_t)(i - i_lo) * (size_t)P.M + (size_t)m] : (R)0;
+            const R Sv = active && in_bounds(P, i - i_lo >= 0 && i - i_lo < P.N)
+                             ? S[(size_t)(i - i_lo) * (size_t)P.M + (size_t)m]
+                             : (R)0;
             V2<R> ph[D];
             start_phases<R, D>(P, i, active ? m : 0, ph);
             fill_powers<R, D>(mypw, K1, BS, ph);
@@ -326,7 +328,8 @@ __global__ void __launch_bounds__(BS) k_project(const __grid_constant__ QrParams
                 sx += (double)a.x;
                 sy += (double)a.y;
             }
-            partial[((size_t)(i - i_lo) * P.n_chunks + ch) * nGp + e] = make_double2(sx, sy);
+            if (in_bounds(P, i - i_lo >= 0 && i - i_lo < P.N && ch >= 0 && ch < P.n_chunks && e < nGp))
+                partial[((size_t)(i - i_lo) * P.n_chunks + ch) * nGp + e] = make_double2(sx, sy);
         }
         __syncthreads();
     }

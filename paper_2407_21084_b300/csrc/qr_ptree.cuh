@@ -260,7 +260,7 @@ __device__ __forceinline__ void project_tree_item(const QrParams& P, const R* __
             sx += (double)sm.acc[w][s].x;
             sy += (double)sm.acc[w][s].y;
         }
-        out[perm[s]] = make_double2(sx, sy);
+        if (in_bounds(P, perm[s] > 0 && perm[s] < P.nGp)) out[perm[s]] = make_double2(sx, sy);
     }
 }
 

@@ -40,6 +40,10 @@ __device__ __forceinline__ void finish_coef(const QrParams& P, double sx, double
     sx /= (double)P.M;
     sy /= (double)P.M;
     if (e == 0) sy = 0.0;
+    diff = 0.0;
+    if (!in_bounds(P, i >= 0 && i <= P.N && e >= 0 && e < P.nGp && zero_idx - e >= 0 && zero_idx + e < nG &&
+                          e < row_stride))
+        return;
     double2* row = alpha + (size_t)i * nG;
     const double2 old = row[zero_idx + e];
     diff = hypot(sx - old.x, sy - old.y);

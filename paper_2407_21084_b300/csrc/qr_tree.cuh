@@ -681,7 +681,8 @@ __device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __res
         const long long m = m0 + p * BS;
         if (m < Pm.M) {
             const R Sv = K.damp ? (gN[p] + sum[p]) * (R)exp((double)-lw0[p]) : gN[p] + sum[p];
-            S[(size_t)(i - i_lo) * (size_t)Pm.M + (size_t)m] = Sv;
+            if (in_bounds(Pm, i - i_lo >= 0 && i - i_lo < Pm.N))
+                S[(size_t)(i - i_lo) * (size_t)Pm.M + (size_t)m] = Sv;
             if (!isfinite(Sv)) ++bad;
         }
     }

@@ -36,6 +36,18 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), name
 
 
+def test_checked_build_exports_the_same_symbols():
+    import ctypes as C
+
+    from paper_2407_21084_b300 import build
+
+    if not os.path.exists(build.LIB_CHECKED):
+        pytest.skip("libqrmc_checked.so not built")
+    lc = C.CDLL(build.LIB_CHECKED)
+    for name in _declared():
+        assert hasattr(lc, name), name
+
+
 def test_sm103a_code_object(lib):
     from paper_2407_21084_b300 import build
 
