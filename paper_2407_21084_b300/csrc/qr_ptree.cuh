@@ -162,12 +162,16 @@ __device__ __forceinline__ R fold32(R (&v)[32], int lane)
     return v[0];
 }
 
+// per block of SC paths: their phases and responses; the block's running
+// sums of every coefficient (one array per CTA: after each tile the warps'
+// folded sums are added in warp order, staged in two buffers by tile parity)
 template <typename R, int D, class TR, int BS, int SC>
 struct ProjSmem {
     static constexpr int W = BS / 32;
     V2<R> z[D][SC];
     R S[SC];
-    V2<R> acc[W][TR::tiles * 32];
+    V2<R> acc[TR::tiles * 32];
+    V2<R> stage[2][W][32];
 };
 
 template <typename R, int D, class TR, int BS, int SC, int T>
@@ -199,9 +203,19 @@ struct Tiles {
                 vi[j] = acc[j].y;
             }
             const R sr = fold32<R>(vr, lane), si = fold32<R>(vi, lane);
-            V2<R>& a = sm.acc[warp][T * 32 + lane];
-            a.x += sr;
-            a.y += si;
+            sm.stage[T & 1][warp][lane] = mk2<R>(sr, si);
+            // the staging buffer of this parity is free: warp 0 summed it
+            // (tile T - 2) before it reached the barrier of tile T - 1
+            __syncthreads();
+            if (warp == 0) {
+                V2<R> a = sm.acc[T * 32 + lane];
+#pragma unroll
+                for (int w = 0; w < BS / 32; ++w) {
+                    a.x += sm.stage[T & 1][w][lane].x;
+                    a.y += sm.stage[T & 1][w][lane].y;
+                }
+                sm.acc[T * 32 + lane] = a;
+            }
             Tiles<R, D, TR, BS, SC, T + 1>::run(sm, warp, lane);
         }
     }
@@ -224,7 +238,7 @@ __device__ __forceinline__ void project_tree_item(const QrParams& P, const R* __
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long base = (long long)ch * P.chunk;
     const long long end = min((long long)P.M, base + P.chunk);
-    for (int t = tid; t < W * TR::tiles * 32; t += BS) (&sm.acc[0][0])[t] = mk2<R>((R)0, (R)0);
+    for (int t = tid; t < TR::tiles * 32; t += BS) sm.acc[t] = mk2<R>((R)0, (R)0);
     R s0 = 0;  // k = 0: sum of the responses (this thread's share)
     for (long long sub = base; sub < end; sub += SC) {
         __syncthreads();
@@ -255,11 +269,7 @@ __device__ __forceinline__ void project_tree_item(const QrParams& P, const R* __
         out[0] = make_double2(t, 0.0);
     }
     for (int s = tid; s < TR::n; s += BS) {
-        double sx = 0.0, sy = 0.0;
-        for (int w = 0; w < W; ++w) {
-            sx += (double)sm.acc[w][s].x;
-            sy += (double)sm.acc[w][s].y;
-        }
+        const double sx = (double)sm.acc[s].x, sy = (double)sm.acc[s].y;
         if (in_bounds(P, perm[s] > 0 && perm[s] < P.nGp)) out[perm[s]] = make_double2(sx, sy);
     }
 }
