@@ -86,9 +86,9 @@ class Solver:
 
     @classmethod
     def from_sec5(cls, p: Sec5Problem, precision=L.QR_FP64, M=None, stream=None, instance=0, path_kernel=0):
-        """The test problem of Sec. 5 (Student nu, min/sin driver and terminal
-        condition, cosine basis, damping exponent p.q), no truncation."""
-        return cls(p.d, p.N, p.T, L.QR_NU_STUDENT2, 2.0, p.gamma_kind, p.gamma_n, p.b, p.sigma,
+        """The test problem of Sec. 5 (Student or Cauchy nu, min/sin driver and
+        terminal condition, cosine basis, damping exponent p.q), no truncation."""
+        return cls(p.d, p.N, p.T, p.nu_kind, p.mu, p.gamma_kind, p.gamma_n, p.b, p.sigma,
                    L.QR_F_PAPER_MIN, p.f_par, L.QR_GT_PAPER_SIN, p.g_par, p.M if M is None else M, p.seed,
                    precision=precision, clamp_L=0.0, stream=stream, instance=instance, path_kernel=path_kernel,
                    damping_q=p.q)

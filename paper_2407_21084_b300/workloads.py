@@ -152,8 +152,9 @@ class Sec5Problem:
     g = 1 + kappa + sin(lam sum x), f = min(1, [y - kappa - 1 - sin(lam sum x)
     e^{lam^2 d (t-T)/2}]^2), exact solution u = 1 + kappa + sin(lam sum x)
     e^{lam^2 d (t-T)/2}; kappa = 0.6, lam = 1/sqrt(d), T = 1; Student nu with
-    mu = 2; cosine basis on an N^d set (Gamma_F, Gamma_T or Gamma_H); damping
-    exponent q of eq. (yqi)."""
+    mu = 2 (nu_kind NU_CAUCHY: mu = 1, the choice of the paper's tables with
+    mixed-derivative damping exponents); cosine basis on an N^d set
+    (Gamma_F, Gamma_T or Gamma_H); damping exponent q of eq. (yqi)."""
 
     d: int
     N: int
@@ -164,6 +165,11 @@ class Sec5Problem:
     T: float = 1.0
     kappa: float = 0.6
     q: float = 0.0  # damping exponent of eq. (yqi)
+    nu_kind: int = NU_STUDENT2  # or NU_CAUCHY
+
+    @property
+    def mu(self) -> float:
+        return 1.0 if self.nu_kind == NU_CAUCHY else 2.0
 
     @property
     def lam(self) -> float:

@@ -30,7 +30,7 @@ def _oracle_problem(ora, p: W.Sec5Problem, M=None):
     K = ora.gamma_list(p.gamma_kind, p.d, p.gamma_n)
     return ora.Problem(d=p.d, N=p.N, T=p.T, k=K, b=p.b, sigma=p.sigma, f_kind=ora.F_PAPER_MIN, f_par=p.f_par,
                        g_kind=ora.GT_PAPER_SIN, g_par=p.g_par, M=p.M if M is None else M, seed=p.seed,
-                       nu_kind=ora.NU_STUDENT2, mu=2.0, basis=ora.BASIS_COS)
+                       nu_kind=p.nu_kind, mu=p.mu, basis=ora.BASIS_COS)
 
 
 def _run(solver, p, prec, kern):

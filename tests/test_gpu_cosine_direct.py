@@ -31,9 +31,18 @@ def _oracle_problem(ora, p: W.Sec5Problem, M=None):
     K = ora.gamma_list(p.gamma_kind, p.d, p.gamma_n)
     op = ora.Problem(d=p.d, N=p.N, T=p.T, k=K, b=p.b, sigma=p.sigma, f_kind=ora.F_PAPER_MIN, f_par=p.f_par,
                      g_kind=ora.GT_PAPER_SIN, g_par=p.g_par, M=p.M if M is None else M, seed=p.seed,
-                     nu_kind=ora.NU_STUDENT2, mu=2.0, basis=ora.BASIS_COS)
+                     nu_kind=p.nu_kind, mu=p.mu, basis=ora.BASIS_COS)
     op.q_damp = p.q
     return op
+
+
+@pytest.mark.parametrize("d,kind,n,N,M,q,precs,nu", [
+    (9, W.G_HYP_N, 5, 2, 110, 17.6, (0,), W.NU_CAUCHY),    # the paper's d = 9 row with mixed-derivative damping
+    (11, W.G_HYP_N, 2, 2, 130, 21.6, (0,), W.NU_CAUCHY),   # and its d = 11 row (Cauchy nu, FP64)
+    (3, W.G_HYP_N, 6, 3, 500, 5.1, (0, 1), W.NU_CAUCHY),
+])
+def test_direct_picard_cauchy_matches_oracle(mods, ora, d, kind, n, N, M, q, precs, nu):
+    test_direct_picard_matches_oracle(mods, ora, d, kind, n, N, M, q, precs, nu)
 
 
 @pytest.mark.parametrize("d,kind,n,N,M,q,precs", [
@@ -51,9 +60,9 @@ def _oracle_problem(ora, p: W.Sec5Problem, M=None):
     (11, W.G_HYP_N, 1, 3, 200, 2.1, (0, 1)),     # {0,1}^11
     (12, W.G_TOTAL_N, 2, 3, 333, 5.1, (0, 1)),   # d = 12, the largest: eleven prefix coordinates
 ])
-def test_direct_picard_matches_oracle(mods, ora, d, kind, n, N, M, q, precs):
+def test_direct_picard_matches_oracle(mods, ora, d, kind, n, N, M, q, precs, nu=W.NU_STUDENT2):
     solver, L = mods
-    p = W.Sec5Problem(d=d, N=N, gamma_kind=kind, gamma_n=n, M=M, seed=21, q=q)
+    p = W.Sec5Problem(d=d, N=N, gamma_kind=kind, gamma_n=n, M=M, seed=21, q=q, nu_kind=nu)
     ref, _ = ora.picard(_oracle_problem(ora, p), 2)
     ref = ref.real
     for prec, tol in ((0, 1e-10), (1, 1e-4)):
