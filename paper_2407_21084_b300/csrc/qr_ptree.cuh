@@ -116,8 +116,11 @@ struct TileSlots {
         constexpr int s = T * 32 + j;
         if constexpr (j < 32 && s < TR::n) {
             if constexpr (TR::pair_at(s)) {
-                // k' +- m e_l: with w = S conj(phi_k') and z_l^m = (a, b),
-                // S conj(phi_{k'+m e}) = w conj(z^m), S conj(phi_{k'-m e}) = w z^m
+                // k' +- m e_l: with w = S conj(phi_k') = p + iq and z_l^m = a + ib,
+                // S conj(phi_{k'+m e}) = w conj(z^m) = (pa + qb) + i(qa - pb) and
+                // S conj(phi_{k'-m e}) = w z^m = (pa - qb) + i(qa + pb): the slots
+                // gather the four sums (pa, qa) and (qb, pb), 4 FMA per path, and
+                // PairForm turns them into the two coefficients per tile pass
                 constexpr int f = TR::nodes.frame[s], dm = TR::nodes.dim[s], m = TR::nodes.pw[s];
                 R p = S, q = (R)0;
                 if constexpr (f >= 0) {
@@ -130,16 +133,37 @@ struct TileSlots {
                     zm = z[dm];
                 else
                     zm = zl[m - 1];
-                acc[j].x = fma(p, zm.x, fma(q, zm.y, acc[j].x));
-                acc[j].y = fma(q, zm.x, fma(-p, zm.y, acc[j].y));
-                acc[j + 1].x = fma(p, zm.x, fma(-q, zm.y, acc[j + 1].x));
-                acc[j + 1].y = fma(q, zm.x, fma(p, zm.y, acc[j + 1].y));
+                acc[j].x = fma(p, zm.x, acc[j].x);
+                acc[j].y = fma(q, zm.x, acc[j].y);
+                acc[j + 1].x = fma(q, zm.y, acc[j + 1].x);
+                acc[j + 1].y = fma(p, zm.y, acc[j + 1].y);
                 TileSlots<R, D, TR, T, j + 2, NP>::run(z, zl, S, acc);
             } else {
                 const V2<R> b = bval<R, D, TR, s>(z);
                 acc[j].x = fma(S, b.x, acc[j].x);
                 acc[j].y = fma(-S, b.y, acc[j].y);  // S conj(phi_k)
                 TileSlots<R, D, TR, T, j + 1, NP>::run(z, zl, S, acc);
+            }
+        }
+    }
+};
+
+// the mirrored pairs of tile T: sums (pa, qa), (qb, pb) -> coefficients
+// ((pa + qb, qa - pb), (pa - qb, qa + pb)) (linear, so it commutes with the
+// sums over paths and lanes that follow)
+template <typename R, class TR, int T, int j>
+struct PairForm {
+    static __device__ __forceinline__ void run(V2<R> (&acc)[32])
+    {
+        constexpr int s = T * 32 + j;
+        if constexpr (j < 32 && s < TR::n) {
+            if constexpr (TR::pair_at(s)) {
+                const V2<R> u = acc[j], v = acc[j + 1];
+                acc[j] = mk2<R>(u.x + v.x, u.y - v.y);
+                acc[j + 1] = mk2<R>(u.x - v.x, u.y + v.y);
+                PairForm<R, TR, T, j + 2>::run(acc);
+            } else {
+                PairForm<R, TR, T, j + 1>::run(acc);
             }
         }
     }
@@ -196,6 +220,7 @@ struct Tiles {
                 for (int mm = 1; mm < NP; ++mm) zl[mm] = cmul<R>(zl[mm - 1], z[D - 1]);
                 TileSlots<R, D, TR, T, 0, NP>::run(z, zl, sm.S[pth], acc);
             }
+            PairForm<R, TR, T, 0>::run(acc);
             R vr[32], vi[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
