@@ -305,10 +305,12 @@ __device__ __forceinline__ R term_g_fast(const QrParams& P, const StepConsts<R, 
 #define QR_TREE_PAIR2 1
 #endif
 
-// subtrees of at most this many slots have both signs unrolled (4: 567 ms
-// against 571 for 8, 598 for 2 or 0, 595 for 16 on the d = 6 workload)
+// subtrees of at most this many slots have both signs unrolled (d = 6
+// workload with the pair forms, where only the first dimensions' subtrees
+// take this branch: 16: 490-492 ms against 499 for 4, 492 for 8 or 32, 496
+// for 2, 574 with every subtree unrolled)
 #ifndef QR_TREE_UNROLL
-#define QR_TREE_UNROLL 4
+#define QR_TREE_UNROLL 16
 #endif
 constexpr int kUnrollSlots = QR_TREE_UNROLL;
 
