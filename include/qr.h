@@ -352,6 +352,20 @@ void qr_mlp_destroy(qr_mlp* m);
 
 /* ---- test hooks (no context) ------------------------------------------ */
 
+/* Host-only test hook: the coefficient layout of the compile-time tree
+ * kernels for the |k|_inf <= n (kind QR_G_LINF) or |k|_1 <= n (QR_G_L1) set
+ * of Z^d, d in [1, 8], n in [1, 31]. Slot s of a packed row is the pair
+ * (x, y) with x = sum_t coef[(2s)T + t] a[idx[(2s)T + t]] and y likewise at
+ * 2s+1, T = *n_terms terms (idx -1: unused), where a is the master row as
+ * 2|Gamma| doubles (re, im of alpha_k in canonical order). The slots follow
+ * the traversal of the kernels: the root, then per dimension the chain
+ * tree in Horner form, +-1 leaf pairs and mirrored chains of the last
+ * dimension as coefficient pairs, the mirrored chains of the
+ * QR_TREE_PAIR_LEVELS dimensions before it as sum and difference subtrees.
+ * Call with idx = coef = NULL for *n_slots; then idx and coef hold
+ * n_slots * 2 * n_terms entries. No device work. */
+qr_status qr_tree_layout(int kind, int d, int n, int* n_slots, int* n_terms, int* idx, double* coef);
+
 /* Philox4x32-10 on the device: ctr_key is n rows of 6 words (ctr0..3, key0,1),
  * out is n rows of 4 words (host arrays). */
 qr_status qr_philox_words(const uint32_t* ctr_key, long long n, uint32_t* out);

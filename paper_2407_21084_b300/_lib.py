@@ -30,6 +30,7 @@ EXPORTS = [
     "qr_last_error", "qr_status_string", "qr_destroy", "qr_philox_words", "qr_sample", "qr_sample_normals_tree", "qr_project_static", "qr_test_points",
     "qr_selftest_wait_timeout",
     "qr_inject_fault",
+    "qr_tree_layout",
     "qr_mlp_create", "qr_mlp_num_params", "qr_mlp_get_params", "qr_mlp_set_params", "qr_mlp_forward",
     "qr_mlp_gradients", "qr_mlp_train_step", "qr_mlp_last_error", "qr_mlp_destroy",
     "qr_batch_create", "qr_batch_picard_step", "qr_batch_info", "qr_batch_set_grouping", "qr_batch_groups",
@@ -201,6 +202,9 @@ def load(path: str | None = None):
     L.qr_selftest_wait_timeout.argtypes = [vp]
     L.qr_inject_fault.restype = C.c_int
     L.qr_inject_fault.argtypes = [vp, C.c_int]
+    L.qr_tree_layout.restype = C.c_int
+    L.qr_tree_layout.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int), dp]
     L.qr_batch_set_grouping.restype = C.c_int
     L.qr_batch_set_grouping.argtypes = [vp, C.c_int]
     L.qr_batch_groups.restype = C.c_int

@@ -1451,6 +1451,26 @@ qr_status qr_test_points(const qr_ctx* ctx, int i, long long n, double* x_out)
     return QR_OK;
 }
 
+qr_status qr_tree_layout(int kind, int d, int n, int* n_slots, int* n_terms, int* idx, double* coef)
+{
+    if ((kind != QR_G_LINF && kind != QR_G_L1) || d < 1 || d > kDMaxFourier || n < 1 || n > 31 || !n_slots)
+        return QR_EINVAL;
+    std::vector<int> K;
+    enumerate_gamma(kind, d, n, K);
+    std::vector<TreeMap> map;
+    if (!build_tree_map(kind, d, n, K, map)) return QR_EINVAL;
+    *n_slots = (int)map.size();
+    if (n_terms) *n_terms = kTreeTerms;
+    for (size_t s = 0; s < map.size(); ++s)
+        for (int h = 0; h < 2; ++h)
+            for (int t = 0; t < kTreeTerms; ++t) {
+                const size_t o = (s * 2 + h) * kTreeTerms + t;
+                if (idx) idx[o] = map[s].c[h][t] != 0.0 ? map[s].i[h][t] : -1;
+                if (coef) coef[o] = map[s].c[h][t];
+            }
+    return QR_OK;
+}
+
 qr_status qr_philox_words(const uint32_t* ctr_key, long long n, uint32_t* out)
 {
     if (n < 0 || (n > 0 && (!ctr_key || !out))) return QR_EINVAL;

@@ -319,6 +319,19 @@ def exchange_group_sums(buf, g_lo: int, g_hi: int, world: int, group=None):
         buf[r * per:(r + 1) * per].copy_(t)
 
 
+def tree_layout(kind: int, d: int, n: int):
+    """The slot map of the compile-time tree kernels (host only, no device):
+    idx (slots, 2, T) int and coef (slots, 2, T) float, see qr_tree_layout."""
+    lib = L.load()
+    ns, nt = C.c_int(), C.c_int()
+    L.check(lib.qr_tree_layout(kind, d, n, C.byref(ns), C.byref(nt), None, None))
+    idx = np.zeros((ns.value, 2, nt.value), dtype=np.int32)
+    coef = np.zeros((ns.value, 2, nt.value))
+    L.check(lib.qr_tree_layout(kind, d, n, C.byref(ns), C.byref(nt), idx.ctypes.data_as(C.POINTER(C.c_int)),
+                               _dp(coef)))
+    return idx, coef
+
+
 def philox_words(ctr_key: np.ndarray) -> np.ndarray:
     """Device Philox4x32-10 on rows (ctr0..3, key0, key1) -> rows of 4 words."""
     lib = L.load()
