@@ -150,11 +150,13 @@ __global__ void __launch_bounds__(BS) k_paths(const __grid_constant__ QrParams P
     __syncthreads();
 
     // rows i+1 .. N are read as series (row N only for a polynomial g)
-    bool inflight[2] = {false, false};
-    uint32_t phase[2] = {0u, 0u};
+    // buffer state in registers, selected by the step parity (indexed arrays
+    // would live in local memory)
+    bool infl0 = false, infl1 = false;
+    uint32_t par0 = 0u, par1 = 0u;
     if (i + 1 < N || (i + 1 == N && trig)) {
         if (tid == 0) bulk_load(abuf[0], packed + (size_t)(i + 1) * row_stride, rowbytes, &bars[0]);
-        inflight[0] = true;
+        infl0 = true;
     }
 
     R x[D];
@@ -179,22 +181,28 @@ __global__ void __launch_bounds__(BS) k_paths(const __grid_constant__ QrParams P
             // ended with a block barrier
             if (tid == 0) {
                 fence_proxy_async_smem();
-                bulk_load(abuf[buf ^ 1], packed + (size_t)nrow * row_stride, rowbytes, &bars[buf ^ 1]);
+                bulk_load((buf ? abuf[0] : abuf[1]), packed + (size_t)nrow * row_stride, rowbytes, &bars[buf ^ 1]);
             }
-            inflight[buf ^ 1] = true;
+            if (buf) infl0 = true;
+            else infl1 = true;
         }
         R z[D], x1[D];
         normals<R, D>(P, i, (uint32_t)m, j, z);
         euler<R, D>(P, x, z, x1);
         R y;
         if (use_series) {
-            const bool ok = mbar_wait(&bars[buf], phase[buf]);
-            phase[buf] ^= 1u;
-            inflight[buf] = false;
+            const bool ok = mbar_wait(&bars[buf], buf ? par1 : par0);
+            if (buf) {
+                par1 ^= 1u;
+                infl1 = false;
+            } else {
+                par0 ^= 1u;
+                infl0 = false;
+            }
             if (!__syncthreads_and(ok)) {
                 if (tid == 0) {
                     atomicOr(status, ST_TIMEOUT);
-                    if (inflight[buf ^ 1]) (void)mbar_wait(&bars[buf ^ 1], phase[buf ^ 1]);
+                    if (buf ? infl0 : infl1) (void)mbar_wait(&bars[buf ^ 1], buf ? par0 : par1);
                 }
                 __syncthreads();
                 return;
@@ -203,7 +211,7 @@ __global__ void __launch_bounds__(BS) k_paths(const __grid_constant__ QrParams P
 #pragma unroll
             for (int l = 0; l < D; ++l) zz[l] = nu_phase<R>(P, x1[l]);
             fill_powers<R, D>(mypw, K1, BS, zz);
-            y = series<R, D>(abuf[buf], tab, first, nGp, mypw, K1, BS);
+            y = series<R, D>((buf ? abuf[1] : abuf[0]), tab, first, nGp, mypw, K1, BS);
             if (damp && row < N) y = undamp<R>(y, damp_logw<R, D>(qh, x1));  // y = ybar^q w(X_{j+1})
             if (row < N && P.clamp_L > 0.0) {
                 const R L = (R)P.clamp_L;

@@ -581,13 +581,19 @@ __device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __res
     const int tid = threadIdx.x, N = Pm.N;
     const bool trig = Pm.g_kind == QR_GT_TRIGPOLY;
     const uint32_t rowbytes = (uint32_t)(row_stride * sizeof(V2<R>));
-    bool inflight[2] = {false, false};
+    // the two buffers' pointers, mbarrier parities and in-flight flags, kept
+    // in registers (selected by the step parity instead of indexed arrays,
+    // which would live in local memory)
+    V2<R>* const buf0 = abuf[0];
+    V2<R>* const buf1 = abuf[1];
+    uint32_t par0 = phase[0], par1 = phase[1];
+    bool infl0 = false, infl1 = false;
     if (i + 1 < N || (i + 1 == N && trig)) {
         if (tid == 0) {
             fence_proxy_async_smem();
-            bulk_load(abuf[0], tree + (size_t)(i + 1) * row_stride, rowbytes, &bars[0]);
+            bulk_load(buf0, tree + (size_t)(i + 1) * row_stride, rowbytes, &bars[0]);
         }
-        inflight[0] = true;
+        infl0 = true;
     }
 
     const StepConsts<R, D> K(Pm);
@@ -604,6 +610,8 @@ __device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __res
 
     for (int j = i; j < N; ++j) {
         const int buf = (j - i) & 1, row = j + 1;
+        V2<R>* const cur = buf ? buf1 : buf0;
+        V2<R>* const nxt = buf ? buf0 : buf1;
         const bool use_series = row < N || trig;
         const int nrow = row + 1;
         R fexp_j;
@@ -614,9 +622,10 @@ __device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __res
         if (nrow < N || (nrow == N && trig)) {
             if (tid == 0) {
                 fence_proxy_async_smem();
-                bulk_load(abuf[buf ^ 1], tree + (size_t)nrow * row_stride, rowbytes, &bars[buf ^ 1]);
+                bulk_load(nxt, tree + (size_t)nrow * row_stride, rowbytes, &bars[buf ^ 1]);
             }
-            inflight[buf ^ 1] = true;
+            if (buf) infl0 = true;
+            else infl1 = true;
         }
         R x1[P][D], y[P];
 #pragma unroll
@@ -626,15 +635,22 @@ __device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __res
             euler_fast<R, D>(K, x[p], z, x1[p]);
         }
         if (use_series) {
-            const bool ok = mbar_wait(&bars[buf], phase[buf]);
-            phase[buf] ^= 1u;
-            inflight[buf] = false;
+            const bool ok = mbar_wait(&bars[buf], buf ? par1 : par0);
+            if (buf) {
+                par1 ^= 1u;
+                infl1 = false;
+            } else {
+                par0 ^= 1u;
+                infl0 = false;
+            }
             if (!__syncthreads_and(ok)) {
                 if (tid == 0) {
                     atomicOr(status, ST_TIMEOUT);
-                    if (inflight[buf ^ 1]) (void)mbar_wait(&bars[buf ^ 1], phase[buf ^ 1]);
+                    if (buf ? infl0 : infl1) (void)mbar_wait(&bars[buf ^ 1], buf ? par0 : par1);
                 }
                 __syncthreads();
+                phase[0] = par0;
+                phase[1] = par1;
                 return false;
             }
             V2<R> zz[P][D];
@@ -642,7 +658,7 @@ __device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __res
             for (int p = 0; p < P; ++p)
 #pragma unroll
                 for (int l = 0; l < D; ++l) zz[p][l] = nu_phase_fast<R>(Pm, x1[p][l]);
-            tree_series<R, D, NN, KIND, P>(abuf[buf], zz, y);
+            tree_series<R, D, NN, KIND, P>(cur, zz, y);
             if (K.damp && row < N) {
 #pragma unroll
                 for (int p = 0; p < P; ++p) y[p] = undamp<R>(y[p], damp_logw<R, D>(K.qh, x1[p]));
@@ -694,6 +710,8 @@ __device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __res
         if (hits) atomicAdd(&counters[CNT_CLAMP], hits);
         if (bad) atomicAdd(&counters[CNT_NONFINITE], bad);
     }
+    phase[0] = par0;
+    phase[1] = par1;
     return true;
 }
 
