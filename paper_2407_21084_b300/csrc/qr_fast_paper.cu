@@ -2,7 +2,9 @@
 // the paper's own experiments (Sec. 5), in their unfolded Z^d form: the
 // one-dimensional Gamma_F(K) with K = 100, 150, 200 (|k| <= K) and the
 // two-dimensional total-degree sets Gamma_T(20, 25, 31) (|k|_1 <= n).
-// Compiled apart to keep build times parallel.
+// Compiled apart to keep build times parallel. The two-dimensional classes
+// need more than 128 registers: 3 resident CTAs per SM here.
+#define QR_TREE_MINB 3
 #include "qr_tree.cuh"
 
 namespace qr {

@@ -716,14 +716,20 @@ __device__ __forceinline__ bool path_item(const QrParams& Pm, const V2<R>* __res
 }
 
 // ------------------------------------------------------ path-and-series kernel
-// resident CTAs per SM the register allocation is held to: 3 gives 168
-// registers and 12 warps per SM without spills for every compiled class; left
-// free, ptxas takes 255 registers (8 warps) and the d = 6 kernel runs 38% slower
+// resident CTAs per SM the register allocation is held to. FP32: 4 (128
+// registers, 16 warps per SM; the d = 6 kernel spills 28 bytes and runs
+// 427 ms against 437.5 at 3 CTAs with 158 registers, 604 at 2 CTAs with
+// three paths per thread); a file whose classes need more registers sets 3
+// before including this header. FP64 (one path per thread): 3. Left free,
+// ptxas takes 255 registers (8 warps per SM).
 #ifndef QR_TREE_MINB
-#define QR_TREE_MINB 3
+#define QR_TREE_MINB 4
+#endif
+#ifndef QR_TREE_MINB64
+#define QR_TREE_MINB64 3
 #endif
 template <typename R, int D, int NN, int KIND, int P, int BS>
-__global__ void __launch_bounds__(BS, QR_TREE_MINB) k_paths_tree(const __grid_constant__ QrParams P_, const V2<R>* __restrict__ tree,
+__global__ void __launch_bounds__(BS, sizeof(R) == 4 ? QR_TREE_MINB : QR_TREE_MINB64) k_paths_tree(const __grid_constant__ QrParams P_, const V2<R>* __restrict__ tree,
                                                    long long row_stride, R* __restrict__ S, int i_lo,
                                                    int tiles_per_i, unsigned long long* __restrict__ counters,
                                                    unsigned* __restrict__ status)
