@@ -59,10 +59,11 @@ int batch_class(int kind, int d, int n)
 
 constexpr int kBatchBS = 128, kBatchP = 2;
 
-// resident CTAs per SM the register allocation is held to (3: 168 registers,
-// a few hundred bytes of spills, still 17% faster than 255 registers at 2 CTAs)
+// resident CTAs per SM the register allocation is held to (4: 128 registers
+// and about 1 KB of spills, 0.770 s per 256-instance iteration against 0.831
+// at 3 CTAs with 168 registers; 2 CTAs without a cap were slower still)
 #ifndef QR_BATCH_MINB
-#define QR_BATCH_MINB 3
+#define QR_BATCH_MINB 4
 #endif
 
 __global__ void __launch_bounds__(kBatchBS, QR_BATCH_MINB) k_paths_batch(const BatchInst* __restrict__ inst,
